@@ -743,23 +743,23 @@ int64_t kxo_exchange_worklist(const kxo_basis* bs, const double* Pm, const int32
     /* ||P_bd||_F per shell pair (user order) */
     double* pq = (double*)malloc(sizeof(double) * (size_t)ns * ns);
     kxo_pblock_sq(bs, Pm, pq);
-    /* group the worklist by A so that one thread owns the K rows of A */
+    /* group the worklist by (A, C): one thread owns the K block of a group */
     int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * 2 * (n_work > 0 ? n_work : 1));
-    for (int64_t w = 0; w < n_work; ++w) { idx[2 * w] = work[4 * w]; idx[2 * w + 1] = w; }
-    qsort(idx, n_work, 2 * sizeof(int64_t), cmp_first);
-    int64_t* seg = (int64_t*)malloc(sizeof(int64_t) * (nl + 1));
-    {
-        int64_t w = 0;
-        for (int A = 0; A <= nl; ++A) {
-            while (w < n_work && idx[2 * w] < A) ++w;
-            seg[A] = w;
-        }
+    for (int64_t w = 0; w < n_work; ++w) {
+        idx[2 * w] = (int64_t)work[4 * w] * nl + work[4 * w + 2];
+        idx[2 * w + 1] = w;
     }
+    qsort(idx, n_work, 2 * sizeof(int64_t), cmp_first);
+    int64_t n_grp = 0;
+    int64_t* grp = (int64_t*)malloc(sizeof(int64_t) * (n_work + 1));
+    for (int64_t w = 0; w < n_work; ++w)
+        if (w == 0 || idx[2 * w] != idx[2 * w - 2]) grp[n_grp++] = w;
+    grp[n_grp] = n_work;
     int64_t total = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
-    for (int A = 0; A < nl; ++A) {
+    for (int64_t g = 0; g < n_grp; ++g) {
         double* buf = (double*)malloc(sizeof(double) * 1296);
-        for (int64_t s = seg[A]; s < seg[A + 1]; ++s) {
+        for (int64_t s = grp[g]; s < grp[g + 1]; ++s) {
             const int32_t* q = work + 4 * idx[2 * s + 1];
             int nA = leaf_node[q[0]], nB = leaf_node[q[1]], nC = leaf_node[q[2]], nD = leaf_node[q[3]];
             for (int ta = lo[nA]; ta < hi[nA]; ++ta) {
@@ -790,6 +790,6 @@ int64_t kxo_exchange_worklist(const kxo_basis* bs, const double* Pm, const int32
         }
         free(buf);
     }
-    free(seg); free(idx); free(pq); free(row_mark); free(leaf_node); free(off);
+    free(grp); free(idx); free(pq); free(row_mark); free(leaf_node); free(off);
     return total;
 }
