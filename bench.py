@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark of the screened exchange build on the (H2O)_64 workload.
+
+One step = one complete exchange build K = sum (mu lam|nu sig) P_{lam sig}
+(P norms and pyramid, pair tables, hextree traversal with the Eq. 8 metric
+query, shell screen, ERI evaluation and contraction) of the seeded
+(H2O)_64 cluster at 1 g/cm^3, medium basis (1984 functions, 1024 shells),
+tau = 1e-10.  The headline is the mixed-precision build (FP32 ERIs for
+quartets with beta <= split, FP64 above), next to the plain FP64 build of
+the same system; both stay within max|dK| <= 1e-8 of the FP64 path.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+Under torchrun every rank builds its own K (replicas: the build of one
+system is not split across GPUs), and the value counts all ranks' builds.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "K-builds/s & ERI quartets/s vs plain FP64 GPU path at max|ΔK|≤1e-8"
+UNIT = "K-builds/s"
+WORKLOAD = "water64"
+TAU = 1e-10
+SPLIT = 1e-5
+L2_FLUSH_BYTES = 256 << 20
+
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+           0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+           0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x100: "display_clocks_setting"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                s = float(parts[0])
+                mx = float(parts[1])
+                bits = int(parts[2], 16) if parts[2].startswith("0x") else int(parts[2])
+            except ValueError:
+                continue
+            sm.append(s)
+            for b, name in REASONS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak(name: str):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f).get(name)
+    except OSError:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(sys_, P, n_rows: int, seed: int = 1):
+    """Exact screened K rows of n_rows sampled shells; returns (seconds,
+    extrapolated K-builds/s, threads, description)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    rows = [int(x) for x in np.random.default_rng(seed).choice(sys_.n_shell, size=n_rows, replace=False)]
+    t0 = time.perf_counter()
+    oracle.exchange_screened(sys_, P, TAU, rows=rows)
+    dt = time.perf_counter() - t0
+    full = dt * sys_.n_shell / n_rows
+    desc = (f"oracle (FP64 C, OpenMP) screened exchange of {n_rows} sampled K-row shells of "
+            f"{sys_.n_shell} ({dt:.1f} s), extrapolated linearly to the full build")
+    return dt, 1.0 / full, oracle.num_threads(), desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as wl
+    sys_, P = wl.workload(WORKLOAD)
+    # warm-up steps and timed steps, each a bounded sample of the workload
+    times = []
+    rates = []
+    threads = 1
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        dt, rate, threads, desc = oracle_sample(sys_, P, args.ref_rows, seed=100 + i)
+        if i >= args.warmup:
+            times.append(dt)
+            rates.append(rate)
+    v = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(sys_, "fp64"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(sys_, precision):
+    return {"workload": f"(H2O)64 water cluster at 1 g/cm^3, even-tempered medium basis "
+                        f"({sys_.n_fn} functions, {sys_.n_shell} shells), tau=1e-10",
+            "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": 10,
+            "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
+            "shell_screen": True,
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB buffer written)",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1401_6961_gb300 as kx
+    import workloads as wl
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kx.load()
+    sys_, P = wl.workload(WORKLOAD)
+    stream = torch.cuda.current_stream(dev)
+    ex = kx.Exchange(sys_, device=local, stream=stream)
+    n = sys_.n_fn
+    Pd = torch.from_numpy(P).to(dev)
+    Kd = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    mixed = dict(tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, profile=1)
+    plain = dict(tau=TAU, precision=kx.KX_FP64, profile=1)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_steps(opts, steps):
+        evs = []
+        launches = 0
+        prof = None
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ex(Pd, out=Kd, **opts)
+            e1.record(stream)
+            evs.append((e0, e1))
+            launches += ex.stats.n_launches
+            p = ex.profile()
+            if prof is None:
+                prof = {k: v.astype(float).copy() for k, v in p.items()}
+            else:
+                for k in prof:
+                    prof[k] += p[k]
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, launches, prof
+
+    # warm-up of the headline path
+    for _ in range(args.warmup):
+        ex(Pd, out=Kd, **mixed)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ms, launches, prof = timed_steps(mixed, args.steps)
+    torch.cuda.synchronize(dev)
+    barrier()
+    st = ex.stats
+    ms = max_over_ranks(ms)
+    ms_step = ms / args.steps
+    value = ws * 1e3 / ms_step
+    quartets = st.n_shell_quartets
+    Kmix = Kd.clone()
+
+    # roofline of the dominant ERI class kernel over the timed steps
+    s_dom = int(np.argmax(prof["ms"]))
+    prec_dom = "fp64" if s_dom < 81 else "fp32"
+    cls = s_dom % 81
+    la, lb, lc, ld = cls // 27, (cls // 9) % 3, (cls // 3) % 3, cls % 3
+    dom_ms = prof["ms"][s_dom]
+    dom_launch = max(prof["launches"][s_dom], 1)
+    achieved = prof["flops"][s_dom] / (dom_ms * 1e-3) / 1e12
+    peak64 = kx.kx_peak_probe(local, kx.KX_FP64) / 1e3
+    peak32 = kx.kx_peak_probe(local, kx.KX_MIXED) / 1e3
+    peak = peak64 if prec_dom == "fp64" else peak32
+    eri_ms = float(prof["ms"].sum())
+    eri_flops64 = float(prof["flops"][:81].sum())
+    eri_flops32 = float(prof["flops"][81:].sum())
+
+    # plain FP64 build of the same system (the speed-up denominator)
+    fp64 = None
+    if args.fp64_steps > 0:
+        ms64, l64, prof64 = timed_steps(plain, args.fp64_steps)
+        ms64 = max_over_ranks(ms64) / args.fp64_steps
+        diff = float((Kmix - Kd).abs().max().item())
+        s64 = int(np.argmax(prof64["ms"]))
+        fp64 = {"value": ws * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+                "warmup": 0, "quartets_per_s": ws * ex.stats.n_shell_quartets / (ms64 * 1e-3),
+                "eri_tflops_fp64": float(prof64["flops"].sum()) / (float(prof64["ms"].sum()) * 1e-3) / 1e12,
+                "eri_frac_of_fp64_peak": float(prof64["flops"].sum()) / (float(prof64["ms"].sum()) * 1e-3)
+                / 1e12 / peak64,
+                "dominant_class": [s64 // 27 % 3, s64 // 9 % 3, s64 // 3 % 3, s64 % 3]}
+    else:
+        diff = None
+
+    # end to end through the host-buffer entry point (pinned host P and K)
+    e2e = None
+    if args.e2e_steps > 0:
+        Ph = torch.from_numpy(P).pin_memory().numpy()
+        Kh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
+        ex.host(Ph, tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(tau=TAU, precision=kx.KX_MIXED,
+                                                               split_threshold=SPLIT), Kh)
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": ws * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
+               "d2h_bytes_per_step": 8 * n * n}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        dt, rate, thr, desc = oracle_sample(sys_, P, args.ref_rows)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": workload_config(sys_, "mixed"),
+            "quartets_per_s": ws * quartets / (ms_step * 1e-3),
+            "shell_quartets": quartets, "leaf_quartets": st.n_leaf_quartets,
+            "shell_quartets_fp64": st.n_shell_quartets_fp64,
+            "stages_ms": {"norms": st.ms_norms, "traverse": st.ms_traverse, "expand": st.ms_expand,
+                          "eri": st.ms_eri},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"k_eri<{la},{lb},{lc},{ld},{'double' if prec_dom == 'fp64' else 'float'}>",
+                         "launches": int(prof["launches"][s_dom]),
+                         "ms_per_launch": dom_ms / dom_launch,
+                         "peak_source": f"measured FMA probe ({prec_dom} pipe), kx_peak_probe"},
+            "eri_stage": {"ms_per_step": eri_ms / args.steps,
+                          "tflops": (eri_flops64 + eri_flops32) / (eri_ms * 1e-3) / 1e12,
+                          "flops_fp64_per_step": eri_flops64 / args.steps,
+                          "flops_fp32_per_step": eri_flops32 / args.steps,
+                          "peak_fp64_tflops": peak64, "peak_fp32_tflops": peak32},
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
+            "max_abs_dK_vs_fp64": diff,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ex.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-rows", type=int, default=2, help="K-row shells per oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

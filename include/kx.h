@@ -1,0 +1,184 @@
+/*
+ * kx.h -- C ABI of the GB300 screened Fock exchange library.
+ *
+ * The library builds the exchange matrix of Challacombe & Bock, "An N-Body
+ * Solution to the Problem of Fock Exchange" (Eqs. 5-6), in the unscaled form
+ *
+ *     K_{mu nu} = sum_{lambda sigma} (mu lambda | nu sigma) P_{lambda sigma}
+ *
+ * (the paper's -1/2 is left to the caller), over uncontracted Cartesian
+ * Gaussian shells (one primitive per shell, l = 0, 1, 2).  Shells are put in
+ * Hilbert-curve order, recursively bisected (Eq. 1), annotated with
+ * Frobenius-norm quadtrees (Eq. 2), and the hextree of Eq. 7 is traversed
+ * level by level on the GPU with the metric query of Eq. 8: a task
+ * (A,B,C,D) -- mu in A, lambda in B, nu in C, sigma in D -- is culled when
+ *
+ *     beta = (||Q_AB||_F * ||P_BD||_F) * ||Q_CD||_F <= tau,
+ *
+ * with Q_{mu lambda} = (mu lambda|mu lambda)^{1/2}.  Surviving shell
+ * quartets are evaluated by McMurchie-Davidson kernels and contracted into K.
+ *
+ * Conventions
+ *   - Cartesian components: x power descending, then y (p: x y z;
+ *     d: xx xy xz yy yz zz).  Each component of a shell carries
+ *     N(a,l) = (2a/pi)^{3/4} (4a)^{l/2} / sqrt((2l-1)!!).
+ *   - Coordinates in bohr, exponents in bohr^-2.
+ *   - Matrices are dense, row-major FP64 in *user* function order (shells in
+ *   input order, functions of a shell contiguous).
+ *   - All device work runs on the stream given to kx_create, in order.
+ *
+ * Errors: every call returns KX_OK or a KX_E* code; kx_last_error() gives a
+ * one-line message.  No call aborts the process, and no call leaves the
+ * CUDA context unusable on an error it detects.  Device waits are bounded.
+ */
+#ifndef KX_H
+#define KX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    KX_OK = 0,
+    KX_EINVAL = 1,     /* bad argument (null pointer, size, l > 2, ...) */
+    KX_ESTATE = 2,     /* called out of order (e.g. exchange before tree) */
+    KX_ENOMEM = 3,     /* device or host allocation failed */
+    KX_ECUDA = 4,      /* a CUDA runtime call failed */
+    KX_ECAPACITY = 5,  /* a caller buffer or a size limit was too small */
+    KX_ETIMEOUT = 6,   /* a bounded device wait gave up */
+    KX_ENOTIMPL = 7    /* option not available in this build */
+};
+
+enum { KX_FP64 = 0, KX_MIXED = 1 };
+
+typedef struct kx_ctx kx_ctx;          /* opaque, owned by the library */
+
+/* Molecule and shell list (host memory, copied by kx_create). */
+typedef struct {
+    int32_t n_atom;
+    int32_t n_shell;             /* 1 .. 65535 */
+    const double* xyz;           /* [n_atom][3] atom centres, bohr */
+    const int32_t* shell_atom;   /* [n_shell] atom of each shell */
+    const int32_t* shell_l;      /* [n_shell] angular momentum, 0..2 */
+    const double* shell_alpha;   /* [n_shell] exponent > 0, bohr^-2 */
+} kx_basis;
+
+/* Options of one exchange build. */
+typedef struct {
+    double tau;                  /* Eq. 8 threshold tau_2e >= 0 (keep iff beta > tau) */
+    double split_threshold;      /* KX_MIXED: shell quartets with beta > split run in FP64 */
+    int32_t precision;           /* KX_FP64 or KX_MIXED */
+    int32_t shell_screen;        /* 1: apply Eq. 8 again to each shell quartet of a leaf */
+    int32_t keep_worklist;       /* 1: retain the leaf-quartet list for kx_get_worklist */
+    int32_t profile;             /* 1: time every ERI class launch (see kx_get_profile) */
+    int64_t chunk_records;       /* shell quartets per evaluation chunk, 0 = default */
+} kx_opts;
+
+/* Counters and stage times of the last build. */
+typedef struct {
+    int64_t n_leaf_quartets;     /* leaf-block quartets surviving Eq. 8 */
+    int64_t n_shell_quartets;    /* shell quartets evaluated */
+    int64_t n_shell_quartets_fp64;
+    int64_t n_candidates;        /* shell quartets screened at the shell level */
+    int64_t n_tasks[32];         /* tasks surviving at each traversal level */
+    int32_t depth;               /* deepest traversal level */
+    int32_t n_chunks;
+    int32_t n_launches;          /* kernels launched by the build */
+    int32_t pad;
+    double flops_fp64;           /* algorithmic FLOPs of the ERI+contraction stage */
+    double flops_fp32;
+    double ms_norms;             /* P norms and pyramid */
+    double ms_traverse;          /* levels 0 .. depth-1 */
+    double ms_expand;            /* last level + shell screen + class binning */
+    double ms_eri;               /* ERI evaluation + contraction */
+    double ms_eri_kernel_max;    /* longest single ERI class launch */
+    double ms_total;
+} kx_stats;
+
+/* Fills the defaults: tau = 1e-10, split 1e-5, FP64, shell screen on,
+ * no worklist retention, default chunking. */
+void kx_default_opts(kx_opts* o);
+
+/* Creates a context on CUDA device `device` (made current by the call) whose
+ * work is ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ * stream).  Copies the basis.  Runs the Hilbert ordering of the atoms
+ * (Sec. "Exchange as hextree traversal": locality-preserving space-filling
+ * curve) on the device.  *out is NULL on failure. */
+int kx_create(kx_ctx** out, const kx_basis* basis, int device, void* cuda_stream);
+
+/* Shell-pair Schwarz factors for Eq. 8: s2(a,b) = sum_{mu in a, lambda in b}
+ * (mu lambda|mu lambda), FP64 on the device.  When tau_ovlp > 0, pairs whose
+ * every overlap |(phi_mu, phi_nu)| is below tau_ovlp are set empty (Eq. 4);
+ * 0 disables that prune.  Geometry-only: call once per context. */
+int kx_build_schwarz(kx_ctx* c, double tau_ovlp);
+
+/* Ragged bisection of the shell index space (Eq. 1) into leaves of at most
+ * leaf_max_functions functions (a single shell is always a leaf; the paper
+ * uses 10), and the Schwarz norm pyramid over it (Eq. 2).  perm, if not
+ * NULL, is a host array [n_shell] giving the user shell at each tree
+ * position and replaces the Hilbert order.  Requires kx_build_schwarz. */
+int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm);
+
+/* One exchange build (Eqs. 6-8).  P and K are DEVICE pointers to row-major
+ * FP64 matrices of n_fn x n_fn in user function order with leading
+ * dimensions ldp, ldk >= n_fn; the caller owns both.  K is overwritten.  P
+ * need not be symmetric.  st may be NULL.  Asynchronous on the context's
+ * stream except for a few small size read-backs. */
+int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
+                double* K, int64_t ldk, kx_stats* st);
+
+/* kx_exchange with HOST buffers: copies P in, builds K, copies K out, and
+ * returns after K is on the host.  Device buffers are cached in the context. */
+int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts* o,
+                     double* K_host, int64_t ldk, kx_stats* st);
+
+/* Number of basis functions. */
+int64_t kx_n_functions(const kx_ctx* c);
+
+/* Tree order: perm[i] = user shell at tree position i (host array). */
+int kx_get_order(const kx_ctx* c, int32_t* perm);
+
+/* Leaves of the bisection, left to right: [lo, hi) tree positions (host
+ * arrays of capacity cap).  *n_leaf and *depth always set. */
+int kx_get_leaves(const kx_ctx* c, int32_t* lo, int32_t* hi, int32_t cap,
+                  int32_t* n_leaf, int32_t* depth);
+
+/* Leaf quartets (A,B,C,D) kept by the last kx_exchange that had
+ * keep_worklist = 1, as leaf ordinals, into host out[cap][4].  With
+ * n_filter > 0 only quartets whose A is in a_filter[] are returned.
+ * *n = number matching (entries beyond cap are not written; KX_ECAPACITY
+ * then).  Order is unspecified. */
+int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter,
+                    int32_t* out, int64_t cap, int64_t* n);
+
+/* Shell-level tables in USER shell order (host arrays [n_shell][n_shell]):
+ * s2 = squared Schwarz norms (after any Eq. 4 prune), pq = squared
+ * Frobenius norms of the P shell blocks of the last kx_exchange (may be
+ * NULL). */
+int kx_get_norms(kx_ctx* c, double* s2, double* pq);
+
+/* Per-stream totals of the last kx_exchange run with profile = 1, for the
+ * 162 streams s = precision * 81 + class (precision 0 = FP64, 1 = FP32;
+ * class = ((la*3 + lb)*3 + lc)*3 + ld): ms = summed CUDA-event time of the
+ * stream's kernel launches, n = shell quartets, flops = algorithmic FLOPs,
+ * launches = kernel launches.  Host arrays of 162 entries (any may be NULL). */
+int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32_t* launches);
+
+/* Throughput probe of the plain FMA pipe on `device`: a kernel of
+ * independent fused multiply-add chains, timed with CUDA events; precision
+ * KX_FP64 or KX_MIXED (= FP32).  *gflops = measured GFLOP/s (2 per FMA).
+ * Not part of the exchange build; used to state roofline fractions. */
+int kx_peak_probe(int device, int precision, double* gflops);
+
+/* Last error message of the context (never NULL). */
+const char* kx_last_error(const kx_ctx* c);
+
+/* Frees the context and all its device memory (NULL is ignored). */
+void kx_destroy(kx_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KX_H */

@@ -1,0 +1,15 @@
+"""GB300-native screened Fock exchange (Challacombe & Bock, "An N-Body
+Solution to the Problem of Fock Exchange").
+
+The library ``libkx.so`` (CUDA, sm_103a) exposes the C ABI of
+``include/kx.h``; this package is its Python binding (``_binding``) and
+build script (``build``).  There is no CPU path: without the built library
+the binding raises.
+"""
+from ._binding import (  # noqa: F401
+    EXPORTS, KX_ECAPACITY, KX_ECUDA, KX_EINVAL, KX_ENOMEM, KX_ENOTIMPL, KX_ESTATE, KX_ETIMEOUT,
+    KX_FP64, KX_MIXED, KX_OK, Exchange, KxError, kx_basis, kx_build_schwarz, kx_build_tree,
+    kx_create, kx_default_opts, kx_destroy, kx_exchange, kx_exchange_host, kx_get_leaves,
+    kx_get_norms, kx_get_order, kx_get_profile, kx_get_worklist, kx_peak_probe, kx_last_error, kx_n_functions, kx_opts,
+    kx_stats, library_path, load,
+)

@@ -1,0 +1,316 @@
+"""ctypes binding of the C ABI in ``include/kx.h``.
+
+Argument marshalling only: every function forwards to the entry point of
+the same name in ``libkx.so``; all computation runs in the library's CUDA
+kernels.  A missing library raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from .build import LIB
+
+KX_OK, KX_EINVAL, KX_ESTATE, KX_ENOMEM, KX_ECUDA, KX_ECAPACITY, KX_ETIMEOUT, KX_ENOTIMPL = range(8)
+KX_FP64, KX_MIXED = 0, 1
+ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "KX_ECUDA",
+               5: "KX_ECAPACITY", 6: "KX_ETIMEOUT", 7: "KX_ENOTIMPL"}
+
+# every entry point declared in include/kx.h
+EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
+           "kx_exchange_host", "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
+           "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_last_error", "kx_destroy"]
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class kx_basis(ctypes.Structure):
+    _fields_ = [("n_atom", ctypes.c_int32), ("n_shell", ctypes.c_int32), ("xyz", _f64p),
+                ("shell_atom", _i32p), ("shell_l", _i32p), ("shell_alpha", _f64p)]
+
+
+class kx_opts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("split_threshold", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("shell_screen", ctypes.c_int32),
+                ("keep_worklist", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("chunk_records", ctypes.c_int64)]
+
+
+class kx_stats(ctypes.Structure):
+    _fields_ = [("n_leaf_quartets", ctypes.c_int64), ("n_shell_quartets", ctypes.c_int64),
+                ("n_shell_quartets_fp64", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("n_tasks", ctypes.c_int64 * 32), ("depth", ctypes.c_int32), ("n_chunks", ctypes.c_int32),
+                ("n_launches", ctypes.c_int32), ("pad", ctypes.c_int32), ("flops_fp64", ctypes.c_double),
+                ("flops_fp32", ctypes.c_double), ("ms_norms", ctypes.c_double),
+                ("ms_traverse", ctypes.c_double), ("ms_expand", ctypes.c_double),
+                ("ms_eri", ctypes.c_double), ("ms_eri_kernel_max", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "n_tasks")}
+        d["n_tasks"] = list(self.n_tasks)[: self.depth + 1]
+        return d
+
+
+class KxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB
+
+
+def load() -> ctypes.CDLL:
+    """Loads libkx.so; raises ImportError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"{LIB} is not built; run paper_1401_6961_gb300.build.build() "
+                          "(the CUDA library is required, there is no CPU path)")
+    L = ctypes.CDLL(LIB)
+    vp = ctypes.c_void_p
+    L.kx_default_opts.argtypes = [ctypes.POINTER(kx_opts)]
+    L.kx_default_opts.restype = None
+    L.kx_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(kx_basis), ctypes.c_int, vp]
+    L.kx_build_schwarz.argtypes = [vp, ctypes.c_double]
+    L.kx_build_tree.argtypes = [vp, ctypes.c_int32, _i32p]
+    L.kx_exchange.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), vp, ctypes.c_int64,
+                              ctypes.POINTER(kx_stats)]
+    L.kx_exchange_host.argtypes = [vp, _f64p, ctypes.c_int64, ctypes.POINTER(kx_opts), _f64p,
+                                   ctypes.c_int64, ctypes.POINTER(kx_stats)]
+    L.kx_n_functions.argtypes = [vp]
+    L.kx_n_functions.restype = ctypes.c_int64
+    L.kx_get_order.argtypes = [vp, _i32p]
+    L.kx_get_leaves.argtypes = [vp, _i32p, _i32p, ctypes.c_int32, _i32p, _i32p]
+    L.kx_get_worklist.argtypes = [vp, _i32p, ctypes.c_int32, _i32p, ctypes.c_int64, _i64p]
+    L.kx_get_norms.argtypes = [vp, _f64p, _f64p]
+    L.kx_get_profile.argtypes = [vp, _f64p, _i64p, _f64p, _i32p]
+    L.kx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _f64p]
+    L.kx_last_error.argtypes = [vp]
+    L.kx_last_error.restype = ctypes.c_char_p
+    L.kx_destroy.argtypes = [vp]
+    L.kx_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("kx_default_opts", "kx_n_functions", "kx_last_error", "kx_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _check(ctx, r: int):
+    if r != KX_OK:
+        msg = load().kx_last_error(ctx).decode() if ctx else "(no context)"
+        raise KxError(r, msg)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one wrapper per entry point
+# ---------------------------------------------------------------------------
+
+def kx_default_opts(**overrides) -> kx_opts:
+    o = kx_opts()
+    load().kx_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class _BasisArrays:
+    def __init__(self, xyz, shell_atom, shell_l, shell_alpha):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self.sa = np.ascontiguousarray(shell_atom, dtype=np.int32)
+        self.sl = np.ascontiguousarray(shell_l, dtype=np.int32)
+        self.al = np.ascontiguousarray(shell_alpha, dtype=np.float64)
+        self.s = kx_basis(self.xyz.shape[0], self.sl.shape[0], _p(self.xyz, _f64p), _p(self.sa, _i32p),
+                          _p(self.sl, _i32p), _p(self.al, _f64p))
+
+
+def kx_create(xyz, shell_atom, shell_l, shell_alpha, device: int = 0, stream: int = 0) -> ctypes.c_void_p:
+    """Context for a basis (bohr, bohr^-2); ``stream`` is a cudaStream_t handle."""
+    b = _BasisArrays(xyz, shell_atom, shell_l, shell_alpha)
+    ctx = ctypes.c_void_p()
+    r = load().kx_create(ctypes.byref(ctx), ctypes.byref(b.s), int(device), ctypes.c_void_p(int(stream)))
+    if r != KX_OK:
+        raise KxError(r, "kx_create failed")
+    return ctx
+
+
+def kx_build_schwarz(ctx, tau_ovlp: float = 0.0) -> None:
+    _check(ctx, load().kx_build_schwarz(ctx, float(tau_ovlp)))
+
+
+def kx_build_tree(ctx, leaf_max_functions: int = 10, perm: Optional[Sequence[int]] = None) -> None:
+    if perm is None:
+        _check(ctx, load().kx_build_tree(ctx, int(leaf_max_functions), None))
+    else:
+        pa = np.ascontiguousarray(perm, dtype=np.int32)
+        _check(ctx, load().kx_build_tree(ctx, int(leaf_max_functions), _p(pa, _i32p)))
+
+
+def kx_exchange(ctx, P_ptr: int, ldp: int, opts: kx_opts, K_ptr: int, ldk: int) -> kx_stats:
+    """Device pointers (ints) to row-major FP64 P and K."""
+    st = kx_stats()
+    _check(ctx, load().kx_exchange(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts),
+                                   ctypes.c_void_p(K_ptr), int(ldk), ctypes.byref(st)))
+    return st
+
+
+def kx_exchange_host(ctx, P: np.ndarray, opts: kx_opts, K: np.ndarray) -> kx_stats:
+    """Host arrays; P and K are row-major float64 (n_fn x n_fn, any ld)."""
+    assert P.dtype == np.float64 and K.dtype == np.float64
+    assert P.flags["C_CONTIGUOUS"] or P.strides[1] == 8
+    st = kx_stats()
+    _check(ctx, load().kx_exchange_host(ctx, P.ctypes.data_as(_f64p), P.strides[0] // 8, ctypes.byref(opts),
+                                        K.ctypes.data_as(_f64p), K.strides[0] // 8, ctypes.byref(st)))
+    return st
+
+
+def kx_n_functions(ctx) -> int:
+    return int(load().kx_n_functions(ctx))
+
+
+def kx_get_order(ctx, n_shell: int) -> np.ndarray:
+    out = np.zeros(n_shell, dtype=np.int32)
+    _check(ctx, load().kx_get_order(ctx, _p(out, _i32p)))
+    return out
+
+
+def kx_get_leaves(ctx) -> Tuple[np.ndarray, int]:
+    """(leaves [n_leaf, 2] of [lo, hi) tree positions, depth)."""
+    nl, dep = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, load().kx_get_leaves(ctx, None, None, 0, ctypes.byref(nl), ctypes.byref(dep)))
+    lo = np.zeros(nl.value, dtype=np.int32)
+    hi = np.zeros(nl.value, dtype=np.int32)
+    _check(ctx, load().kx_get_leaves(ctx, _p(lo, _i32p), _p(hi, _i32p), nl.value, ctypes.byref(nl),
+                                     ctypes.byref(dep)))
+    return np.stack([lo, hi], axis=1), int(dep.value)
+
+
+def kx_get_worklist(ctx, a_filter: Optional[Sequence[int]] = None, cap: int = 1 << 22) -> np.ndarray:
+    L = load()
+    fa = np.ascontiguousarray(a_filter if a_filter is not None else [], dtype=np.int32)
+    n = ctypes.c_int64()
+    while True:
+        out = np.zeros((max(cap, 1), 4), dtype=np.int32)
+        r = L.kx_get_worklist(ctx, _p(fa, _i32p), int(fa.shape[0]), _p(out, _i32p), int(cap), ctypes.byref(n))
+        if r == KX_ECAPACITY:
+            cap = int(n.value)
+            continue
+        _check(ctx, r)
+        return out[: n.value].copy()
+
+
+def kx_get_norms(ctx, n_shell: int, with_p: bool = True) -> Tuple[np.ndarray, Optional[np.ndarray]]:
+    s2 = np.zeros((n_shell, n_shell))
+    pq = np.zeros((n_shell, n_shell)) if with_p else None
+    _check(ctx, load().kx_get_norms(ctx, _p(s2, _f64p), _p(pq, _f64p) if with_p else None))
+    return s2, pq
+
+
+def kx_get_profile(ctx) -> dict:
+    """Per-stream totals of the last profiled build: arrays of 162 entries
+    indexed by precision * 81 + class (precision 0 = FP64)."""
+    ms = np.zeros(162)
+    n = np.zeros(162, dtype=np.int64)
+    fl = np.zeros(162)
+    la = np.zeros(162, dtype=np.int32)
+    _check(ctx, load().kx_get_profile(ctx, _p(ms, _f64p), _p(n, _i64p), _p(fl, _f64p), _p(la, _i32p)))
+    return {"ms": ms, "n": n, "flops": fl, "launches": la}
+
+
+def kx_peak_probe(device: int = 0, precision: int = KX_FP64) -> float:
+    """Measured FMA-pipe throughput in GFLOP/s (FP64 or, with KX_MIXED, FP32)."""
+    g = ctypes.c_double()
+    r = load().kx_peak_probe(int(device), int(precision), ctypes.byref(g))
+    if r != KX_OK:
+        raise KxError(r, "kx_peak_probe failed")
+    return float(g.value)
+
+
+def kx_last_error(ctx) -> str:
+    return load().kx_last_error(ctx).decode()
+
+
+def kx_destroy(ctx) -> None:
+    if ctx:
+        load().kx_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience object over torch tensors
+# ---------------------------------------------------------------------------
+
+class Exchange:
+    """A context for one molecule: ``Exchange(system)(P) -> K`` on the GPU.
+
+    ``system`` has ``xyz`` (bohr), ``shell_atom``, ``shell_l`` and
+    ``shell_alpha`` (bohr^-2), e.g. a ``workloads.System``.
+    """
+
+    def __init__(self, system, device: int = 0, leaf_max: int = 10, tau_ovlp: float = 0.0,
+                 perm=None, stream=None):
+        import torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.n_shell = int(len(system.shell_l))
+        self.ctx = kx_create(system.xyz, system.shell_atom, system.shell_l, system.shell_alpha,
+                             device, self.stream.cuda_stream)
+        self.n_fn = kx_n_functions(self.ctx)
+        kx_build_schwarz(self.ctx, tau_ovlp)
+        kx_build_tree(self.ctx, leaf_max, perm)
+
+    def __call__(self, P, out=None, **opts):
+        import torch
+        assert P.is_cuda and P.dtype == torch.float64 and P.stride(1) == 1
+        n = self.n_fn
+        assert P.shape == (n, n)
+        K = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=P.device)
+        o = kx_default_opts(**opts)
+        self.stats = kx_exchange(self.ctx, P.data_ptr(), P.stride(0), o, K.data_ptr(), K.stride(0))
+        return K
+
+    def host(self, P: np.ndarray, **opts) -> np.ndarray:
+        K = np.zeros_like(P)
+        self.stats = kx_exchange_host(self.ctx, np.ascontiguousarray(P), kx_default_opts(**opts), K)
+        return K
+
+    def worklist(self, a_filter=None) -> np.ndarray:
+        return kx_get_worklist(self.ctx, a_filter)
+
+    def order(self) -> np.ndarray:
+        return kx_get_order(self.ctx, self.n_shell)
+
+    def leaves(self):
+        return kx_get_leaves(self.ctx)
+
+    def profile(self) -> dict:
+        return kx_get_profile(self.ctx)
+
+    def norms(self, with_p: bool = True):
+        return kx_get_norms(self.ctx, self.n_shell, with_p)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            kx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

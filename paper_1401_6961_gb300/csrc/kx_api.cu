@@ -1,0 +1,353 @@
+// kx_api.cu -- the C ABI declared in include/kx.h.  Argument checks, call
+// order, device selection and host marshalling live here; every step of the
+// computation runs in the kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "kx_internal.cuh"
+
+using namespace kx;
+
+namespace {
+
+// Makes the context's device current for the duration of a call and puts
+// the caller's device back afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) (void)cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+__global__ void k_filter_work(const Task* __restrict__ w, int64_t n, const uint8_t* __restrict__ amark,
+                              Task* __restrict__ out, unsigned long long* __restrict__ cnt, int64_t cap) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Task t = w[i];
+        if (amark && !amark[t.a]) continue;
+        unsigned long long pos = atomicAdd(cnt, 1ull);
+        if ((int64_t)pos < cap) out[pos] = t;
+    }
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int check_ctx(const kx_ctx* c) { return c ? KX_OK : KX_EINVAL; }
+
+void free_all(kx_ctx* c) {
+    void* ptrs[] = {c->d_tl, c->d_tctr, c->d_talpha, c->d_tfoff, c->d_perm, c->d_s2, c->d_snorm, c->d_slog,
+                    c->d_pq, c->d_pnorm, c->d_plog, c->d_node_lo, c->d_node_hi, c->d_node_child,
+                    c->d_node_nchild, c->d_sq_s, c->d_sq_p, c->d_nrm_s, c->d_nrm_p, c->d_leaf_lo, c->d_leaf_hi,
+                    c->d_boys64, c->d_boys32, c->d_pairmap, c->d_scratch, c->d_front[0], c->d_front[1],
+                    c->d_mask, c->d_scan, c->d_rec, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
+                    c->d_hostP, c->d_hostK};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < NPAIRCLASS; ++i) {
+        if (c->d_pairmeta[i]) cudaFree(c->d_pairmeta[i]);
+        if (c->d_pair64[i]) cudaFree(c->d_pair64[i]);
+        if (c->d_pair32[i]) cudaFree(c->d_pair32[i]);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void kx_default_opts(kx_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tau = 1e-10;
+    o->split_threshold = 1e-5;
+    o->precision = KX_FP64;
+    o->shell_screen = 1;
+    o->keep_worklist = 0;
+    o->profile = 0;
+    o->chunk_records = 0;
+}
+
+int kx_create(kx_ctx** out, const kx_basis* b, int device, void* cuda_stream) {
+    if (!out) return KX_EINVAL;
+    *out = nullptr;
+    if (!b || !b->xyz || !b->shell_atom || !b->shell_l || !b->shell_alpha) return KX_EINVAL;
+    if (b->n_atom <= 0 || b->n_shell <= 0 || b->n_shell > 65535) return KX_EINVAL;
+    for (int i = 0; i < 3 * b->n_atom; ++i)
+        if (!std::isfinite(b->xyz[i])) return KX_EINVAL;
+    for (int s = 0; s < b->n_shell; ++s) {
+        if (b->shell_atom[s] < 0 || b->shell_atom[s] >= b->n_atom) return KX_EINVAL;
+        if (b->shell_l[s] < 0 || b->shell_l[s] > LMAX) return KX_EINVAL;
+        if (!finite_pos(b->shell_alpha[s])) return KX_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        (void)cudaGetLastError();
+        return KX_ECUDA;
+    }
+    kx_ctx* c = new (std::nothrow) kx_ctx();
+    if (!c) return KX_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    if (!g.ok) {
+        delete c;
+        return KX_ECUDA;
+    }
+    c->n_atom = b->n_atom;
+    c->n_shell = b->n_shell;
+    c->xyz.assign(b->xyz, b->xyz + 3 * (size_t)b->n_atom);
+    c->shell_atom.assign(b->shell_atom, b->shell_atom + b->n_shell);
+    c->shell_l.assign(b->shell_l, b->shell_l + b->n_shell);
+    c->shell_alpha.assign(b->shell_alpha, b->shell_alpha + b->n_shell);
+    c->fn_off.resize(b->n_shell + 1);
+    c->fn_off[0] = 0;
+    for (int s = 0; s < b->n_shell; ++s) c->fn_off[s + 1] = c->fn_off[s] + ncart(b->shell_l[s]);
+    c->n_fn = c->fn_off[b->n_shell];
+    int r = KX_OK;
+    cudaError_t e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * NCOUNTERS);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * NCOUNTERS, c->stream);
+    if (e != cudaSuccess) r = cuda_check(c, e, "kx_create");
+    if (r == KX_OK) r = boys_table(c);
+    if (r == KX_OK) r = order_atoms(c);
+    if (r != KX_OK) {
+        free_all(c);
+        delete c;
+        return r;
+    }
+    *out = c;
+    return KX_OK;
+}
+
+int kx_build_schwarz(kx_ctx* c, double tau_ovlp) {
+    KX_TRY(check_ctx(c));
+    if (!std::isfinite(tau_ovlp) || tau_ovlp < 0.0) return set_err(c, KX_EINVAL, "tau_ovlp must be >= 0");
+    if (!c->have_order) return set_err(c, KX_ESTATE, "no shell order");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    c->tau_ovlp = tau_ovlp;
+    c->have_tree = false;
+    return schwarz(c, tau_ovlp);
+}
+
+int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm) {
+    KX_TRY(check_ctx(c));
+    if (leaf_max_functions < 1) return set_err(c, KX_EINVAL, "leaf_max_functions must be >= 1");
+    if (!c->have_schwarz) return set_err(c, KX_ESTATE, "kx_build_schwarz must come first");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    if (perm) {
+        std::vector<char> seen(c->n_shell, 0);
+        for (int i = 0; i < c->n_shell; ++i) {
+            if (perm[i] < 0 || perm[i] >= c->n_shell || seen[perm[i]])
+                return set_err(c, KX_EINVAL, "perm is not a permutation of the shells");
+            seen[perm[i]] = 1;
+        }
+        c->perm.assign(perm, perm + c->n_shell);
+        KX_CUDA(c, cudaMemcpyAsync(c->d_perm, c->perm.data(), sizeof(int32_t) * c->n_shell,
+                                   cudaMemcpyHostToDevice, c->stream));
+        // the Schwarz table is kept in tree order: rebuild it for the new order
+        KX_TRY(schwarz(c, c->tau_ovlp));
+    }
+    c->have_tree = false;
+    c->keep_valid = false;
+    return build_tree(c, leaf_max_functions);
+}
+
+int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+                kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
+    if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
+    if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
+    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
+        return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
+    if (o->chunk_records < 0) return set_err(c, KX_EINVAL, "chunk_records must be >= 0");
+    if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    kx_stats local;
+    kx_stats* s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
+    int r = traverse_and_evaluate(c, P, ldp, o, K, ldk, s);
+    cudaEventRecord(e1, c->stream);
+    if (r == KX_OK) {
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) r = cuda_check(c, e, "kx_exchange");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        s->ms_total = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r;
+}
+
+int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts* o, double* K_host, int64_t ldk,
+                     kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P_host || !K_host || !o) return set_err(c, KX_EINVAL, "null argument");
+    if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    size_t n = (size_t)c->n_fn;
+    if (c->host_cap < n * n) {
+        cudaFree(c->d_hostP);
+        cudaFree(c->d_hostK);
+        c->d_hostP = c->d_hostK = nullptr;
+        c->host_cap = 0;
+        KX_CUDA(c, cudaMalloc(&c->d_hostP, sizeof(double) * n * n));
+        KX_CUDA(c, cudaMalloc(&c->d_hostK, sizeof(double) * n * n));
+        c->host_cap = n * n;
+    }
+    KX_CUDA(c, cudaMemcpy2DAsync(c->d_hostP, sizeof(double) * n, P_host, sizeof(double) * ldp, sizeof(double) * n, n,
+                                 cudaMemcpyHostToDevice, c->stream));
+    KX_TRY(kx_exchange(c, c->d_hostP, (int64_t)n, o, c->d_hostK, (int64_t)n, st));
+    KX_CUDA(c, cudaMemcpy2DAsync(K_host, sizeof(double) * ldk, c->d_hostK, sizeof(double) * n, sizeof(double) * n, n,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KX_OK;
+}
+
+int64_t kx_n_functions(const kx_ctx* c) { return c ? c->n_fn : -1; }
+
+int kx_get_order(const kx_ctx* c, int32_t* perm) {
+    if (!c || !perm) return KX_EINVAL;
+    if (!c->have_order) return KX_ESTATE;
+    std::memcpy(perm, c->perm.data(), sizeof(int32_t) * c->n_shell);
+    return KX_OK;
+}
+
+int kx_get_leaves(const kx_ctx* c, int32_t* lo, int32_t* hi, int32_t cap, int32_t* n_leaf, int32_t* depth) {
+    if (!c || !n_leaf || !depth) return KX_EINVAL;
+    if (!c->have_tree) return KX_ESTATE;
+    const int D = c->depth, nl = c->levels[D].n, off = c->levels[D].off;
+    *n_leaf = nl;
+    *depth = D;
+    if (!lo || !hi) return KX_OK;
+    if (cap < nl) return KX_ECAPACITY;
+    std::memcpy(lo, c->node_lo.data() + off, sizeof(int32_t) * nl);
+    std::memcpy(hi, c->node_hi.data() + off, sizeof(int32_t) * nl);
+    return KX_OK;
+}
+
+int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter, int32_t* out, int64_t cap, int64_t* n) {
+    KX_TRY(check_ctx(c));
+    if (!n || (n_filter > 0 && !a_filter) || n_filter < 0 || cap < 0 || (cap > 0 && !out))
+        return set_err(c, KX_EINVAL, "bad argument");
+    if (!c->keep_valid) return set_err(c, KX_ESTATE, "no worklist kept (set keep_worklist)");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    const int nl = c->levels[c->depth].n;
+    uint8_t* d_mark = nullptr;
+    Task* d_out = nullptr;
+    unsigned long long* d_cnt = c->d_counters + CTR_FILTER;
+    int r = KX_OK;
+    cudaError_t e = cudaSuccess;
+    if (n_filter > 0) {
+        std::vector<uint8_t> mark(nl, 0);
+        for (int i = 0; i < n_filter; ++i)
+            if (a_filter[i] >= 0 && a_filter[i] < nl) mark[a_filter[i]] = 1;
+        e = cudaMalloc(&d_mark, nl);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_mark, mark.data(), nl, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess && cap > 0) e = cudaMalloc(&d_out, sizeof(Task) * cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
+    unsigned long long cnt = 0;
+    if (e == cudaSuccess && c->keep_n > 0) {
+        unsigned grid = (unsigned)std::min<size_t>((c->keep_n + 255) / 256, 152 * 32);
+        k_filter_work<<<grid, 256, 0, c->stream>>>(c->d_keep, (int64_t)c->keep_n, d_mark, d_out, d_cnt, cap);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+        *n = (int64_t)cnt;
+        int64_t m = std::min<int64_t>((int64_t)cnt, cap);
+        if (m > 0) {
+            std::vector<Task> h(m);
+            e = cudaMemcpy(h.data(), d_out, sizeof(Task) * m, cudaMemcpyDeviceToHost);
+            for (int64_t i = 0; i < m; ++i) {
+                out[4 * i] = h[i].a;
+                out[4 * i + 1] = h[i].b;
+                out[4 * i + 2] = h[i].c;
+                out[4 * i + 3] = h[i].d;
+            }
+        }
+        if (e == cudaSuccess && (int64_t)cnt > cap) r = set_err(c, KX_ECAPACITY, "worklist larger than cap");
+    }
+    if (e != cudaSuccess) r = cuda_check(c, e, "kx_get_worklist");
+    cudaFree(d_mark);
+    cudaFree(d_out);
+    return r;
+}
+
+int kx_get_norms(kx_ctx* c, double* s2, double* pq) {
+    KX_TRY(check_ctx(c));
+    if (!c->have_schwarz) return set_err(c, KX_ESTATE, "kx_build_schwarz must come first");
+    if (pq && !c->have_pq) return set_err(c, KX_ESTATE, "no P norms (run kx_exchange)");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    const int ns = c->n_shell;
+    std::vector<double> t((size_t)ns * ns);
+    const double* src[2] = {c->d_s2, c->d_pq};
+    double* dst[2] = {s2, pq};
+    for (int k = 0; k < 2; ++k) {
+        if (!dst[k]) continue;
+        KX_CUDA(c, cudaMemcpy(t.data(), src[k], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < ns; ++i)
+            for (int j = 0; j < ns; ++j) dst[k][(size_t)c->perm[i] * ns + c->perm[j]] = t[(size_t)i * ns + j];
+    }
+    return KX_OK;
+}
+
+int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32_t* launches) {
+    if (!c) return KX_EINVAL;
+    for (int s = 0; s < 2 * NCLASS; ++s) {
+        if (ms) ms[s] = c->prof_ms[s];
+        if (n) n[s] = c->prof_n[s];
+        if (flops) flops[s] = c->prof_flops[s];
+        if (launches) launches[s] = c->prof_launches[s];
+    }
+    return KX_OK;
+}
+
+int kx_peak_probe(int device, int precision, double* gflops) {
+    if (!gflops || (precision != KX_FP64 && precision != KX_MIXED)) return KX_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        (void)cudaGetLastError();
+        return KX_ECUDA;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) return KX_ECUDA;
+    return peak_probe(device, precision, gflops);
+}
+
+const char* kx_last_error(const kx_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void kx_destroy(kx_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        if (g.ok) {
+            cudaStreamSynchronize(c->stream);
+            free_all(c);
+        }
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,846 @@
+// kx_eri_impl.cuh -- McMurchie-Davidson shell-quartet kernels, one
+// instantiation per angular-momentum class (la,lb,lc,ld) and precision.
+//
+// One thread evaluates one surviving shell quartet (a,b,c,d) (the leaf
+// contractions of Eq. 7 restricted to the quartets that pass Eq. 8) and
+// contracts it straight into its K block,
+//
+//   K_{mu nu} += sum_{lam in b, sig in d} (mu lam|nu sig) P_{lam sig},
+//   (mu lam|nu sig) = pref * sum_{h in bra} E^{ab}_{mu lam,h}
+//                      sum_{h' in ket} (-1)^{|h'|} E^{cd}_{nu sig,h'} R_{h+h'},
+//
+// with Hermite indices h = (t,u,v).  R_{tuv} comes from the Boys function
+// F_n(T), T = rho |P-Q|^2, by the usual Hermite recursion.  The contraction
+// with P is folded into the Hermite-to-Cartesian transform, in whichever of
+// two orders has the smaller middle (R-contraction) step:
+//   order A (loop nu, lam):  T_{h'} = sum_sig E^{cd}_{nu sig,h'} P_{lam sig},
+//                            U_h = sum_{h'} (-1)^{|h'|} R_{h+h'} T_{h'},
+//                            K_{mu nu} += sum_h E^{ab}_{mu lam,h} U_h;
+//   order B (loop mu, sig):  W_h = sum_lam E^{ab}_{mu lam,h} P_{lam sig},
+//                            V_{h'} = sum_h R_{h+h'} W_h,
+//                            K_{mu nu} += sum_{h'} (-1)^{|h'|} E^{cd}_{nu sig,h'} V_{h'}.
+// Every loop is a compile-time loop, so all Hermite and Cartesian indices
+// are constants and the intermediates live in registers.  Per-thread K
+// partials are reduced across the warp over runs of equal (a,c) before the
+// FP64 atomic add into K.
+#pragma once
+
+#include <utility>
+
+#include "kx_internal.cuh"
+
+namespace kx {
+
+// ---------------------------------------------------------------------------
+// compile-time loops
+// ---------------------------------------------------------------------------
+
+template <int N>
+using ic = std::integral_constant<int, N>;
+
+template <typename F, int... I>
+__device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(ic<I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+    if constexpr (N > 0) sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+#define KX_CV(x) decltype(x)::value
+
+__host__ __device__ constexpr int imax0(int x) { return x > 0 ? x : 0; }
+
+// h = (t,u,v) is reached by some component pair whose first member has the
+// fixed powers (x,y,z) and whose second member has total l2:
+// sum of the excesses over (x,y,z) must not exceed l2.
+__host__ __device__ constexpr bool reach(int t, int u, int v, int x, int y, int z, int l2) {
+    return imax0(t - x) + imax0(u - y) + imax0(v - z) <= l2;
+}
+
+// ---------------------------------------------------------------------------
+// precision traits
+// ---------------------------------------------------------------------------
+
+template <typename R>
+struct Real;
+template <>
+struct Real<double> {
+    __device__ static double sqrt_(double x) { return sqrt(x); }
+    __device__ static double exp_(double x) { return exp(x); }
+    __device__ static int rnd(double x) { return __double2int_rn(x); }
+};
+template <>
+struct Real<float> {
+    __device__ static float sqrt_(float x) { return sqrtf(x); }
+    __device__ static float exp_(float x) { return expf(x); }
+    __device__ static int rnd(float x) { return __float2int_rn(x); }
+};
+
+// FP32 -> FP64 by bit manipulation (integer pipe), subnormals flushed.
+__device__ __forceinline__ double f2d_bits(float f) {
+    uint32_t u = __float_as_uint(f);
+    uint32_t e = (u >> 23) & 0xffu;
+    uint64_t s = (uint64_t)(u & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)s);
+    uint64_t m = (uint64_t)(u & 0x7fffffu) << 29;
+    uint64_t ee = (e == 0xffu) ? 0x7ffull : (uint64_t)(e + 896u);
+    return __longlong_as_double((long long)(s | (ee << 52) | m));
+}
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+
+// ---------------------------------------------------------------------------
+// Boys function and Hermite integrals
+// ---------------------------------------------------------------------------
+
+// G_n = pref (-2 rho)^n F_n(T), n = 0..L.
+// T < BOYS_TMAX: seven-term Taylor series about the nearest grid point,
+//   F_m(T_i + d) = sum_k (-d)^k / k! F_{m+k}(T_i).
+// T >= BOYS_TMAX: F_0 = (1/2) sqrt(pi/T) (erfc(sqrt T) < 1e-18 there) and
+//   the upward recursion F_{m+1} = ((2m+1) F_m - e^{-T}) / (2T), stable for
+//   2m+1 < 2T; in FP32 the e^{-T} term is below the rounding unit and the
+//   scaled form G_{n+1} = -G_n (2n+1) / |P-Q|^2 avoids underflow.
+template <int L, typename R>
+__device__ __forceinline__ void boys_scaled(R* G, R T, R rho, R r2, R pref, const R* __restrict__ tab) {
+    if (T < R(BOYS_TMAX)) {
+        int ig = Real<R>::rnd(T * R(BOYS_DENS));
+        R d = T - R(ig) * R(1.0 / BOYS_DENS);
+        const R* row = tab + ig * (BOYS_M + 1);
+        R md[6];
+        sfor<6>([&](auto k_) {
+            constexpr int k = KX_CV(k_);
+            md[k] = -d * R(1.0 / (k + 1));
+        });
+        R s = pref;
+        const R m2r = R(-2) * rho;
+        sfor<L + 1>([&](auto m_) {
+            constexpr int m = KX_CV(m_);
+            R acc = __ldg(row + m + 6);
+            sfor<6>([&](auto k_) {
+                constexpr int k = 5 - KX_CV(k_);
+                acc = __ldg(row + m + k) + acc * md[k];
+            });
+            G[m] = s * acc;
+            if constexpr (m < L) s *= m2r;
+        });
+    } else {
+        R f0 = R(0.5) * Real<R>::sqrt_(R(PI) / T);
+        if constexpr (sizeof(R) == 8) {
+            R e = Real<R>::exp_(-T);
+            R inv2t = R(0.5) / T;
+            R F = f0, s = pref;
+            const R m2r = R(-2) * rho;
+            sfor<L + 1>([&](auto m_) {
+                constexpr int m = KX_CV(m_);
+                G[m] = s * F;
+                if constexpr (m < L) {
+                    F = (R(2 * m + 1) * F - e) * inv2t;
+                    s *= m2r;
+                }
+            });
+        } else {
+            R inv_r2 = R(1) / r2;
+            R g = pref * f0;
+            sfor<L + 1>([&](auto m_) {
+                constexpr int m = KX_CV(m_);
+                G[m] = g;
+                if constexpr (m < L) g *= R(-(2 * m + 1)) * inv_r2;
+            });
+        }
+    }
+}
+
+// R_{tuv} (n = 0) for t+u+v <= L, in place from the highest n down:
+//   R^n_{t,u,v} = (t-1) R^{n+1}_{t-2,u,v} + X R^{n+1}_{t-1,u,v}  (t > 0),
+// likewise in u (t = 0) and v (t = u = 0); R^n_{000} = G_n.
+template <int L, typename R>
+__device__ __forceinline__ void hermite_r(R* Rt, const R* G, R X, R Y, R Z) {
+    Rt[0] = G[L];
+    sfor<L>([&](auto k_) {
+        constexpr int n = L - 1 - KX_CV(k_);
+        sfor<L - n>([&](auto j_) {
+            constexpr int j = L - n - KX_CV(j_);
+            sfor<j + 1>([&](auto t_) {
+                constexpr int t = KX_CV(t_);
+                sfor<j - t + 1>([&](auto u_) {
+                    constexpr int u = KX_CV(u_);
+                    constexpr int v = j - t - u;
+                    if constexpr (t > 0) {
+                        R r = X * Rt[hidx(t - 1, u, v)];
+                        if constexpr (t > 1) r += R(t - 1) * Rt[hidx(t - 2, u, v)];
+                        Rt[hidx(t, u, v)] = r;
+                    } else if constexpr (u > 0) {
+                        R r = Y * Rt[hidx(t, u - 1, v)];
+                        if constexpr (u > 1) r += R(u - 1) * Rt[hidx(t, u - 2, v)];
+                        Rt[hidx(t, u, v)] = r;
+                    } else {
+                        R r = Z * Rt[hidx(t, u, v - 1)];
+                        if constexpr (v > 1) r += R(v - 1) * Rt[hidx(t, u, v - 2)];
+                        Rt[hidx(t, u, v)] = r;
+                    }
+                });
+            });
+        });
+        Rt[0] = G[n];
+    });
+}
+
+// ---------------------------------------------------------------------------
+// contraction orders
+// ---------------------------------------------------------------------------
+
+// cost of the R-contraction step of each order (multiply-adds)
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr int mid_cost(bool orderA) {
+    int n = 0;
+    if (orderA) {
+        for (int nu = 0; nu < ncart(LC); ++nu)
+            for (int lam = 0; lam < ncart(LB); ++lam) {
+                int nh = 0, nh2 = 0;
+                for (int t = 0; t <= LA + LB; ++t)
+                    for (int u = 0; t + u <= LA + LB; ++u)
+                        for (int v = 0; t + u + v <= LA + LB; ++v)
+                            nh += reach(t, u, v, cart_x(LB, lam), cart_y(LB, lam), cart_z(LB, lam), LA);
+                for (int t = 0; t <= LC + LD; ++t)
+                    for (int u = 0; t + u <= LC + LD; ++u)
+                        for (int v = 0; t + u + v <= LC + LD; ++v)
+                            nh2 += reach(t, u, v, cart_x(LC, nu), cart_y(LC, nu), cart_z(LC, nu), LD);
+                n += nh * nh2;
+            }
+    } else {
+        for (int mu = 0; mu < ncart(LA); ++mu)
+            for (int sig = 0; sig < ncart(LD); ++sig) {
+                int nh = 0, nh2 = 0;
+                for (int t = 0; t <= LA + LB; ++t)
+                    for (int u = 0; t + u <= LA + LB; ++u)
+                        for (int v = 0; t + u + v <= LA + LB; ++v)
+                            nh += reach(t, u, v, cart_x(LA, mu), cart_y(LA, mu), cart_z(LA, mu), LB);
+                for (int t = 0; t <= LC + LD; ++t)
+                    for (int u = 0; t + u <= LC + LD; ++u)
+                        for (int v = 0; t + u + v <= LC + LD; ++v)
+                            nh2 += reach(t, u, v, cart_x(LD, sig), cart_y(LD, sig), cart_z(LD, sig), LC);
+                n += nh * nh2;
+            }
+    }
+    return n;
+}
+
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr bool use_order_a() {
+    return mid_cost<LA, LB, LC, LD>(true) <= mid_cost<LA, LB, LC, LD>(false);
+}
+
+// order A: loop nu in c, lam in b
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void contract_a(R* kacc, const R* Rt, const R* eab, const R* ecd,
+                                           const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD;
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    sfor<NC>([&](auto inu_) {
+        constexpr int inu = KX_CV(inu_);
+        constexpr int nx = cart_x(LC, inu), ny = cart_y(LC, inu), nz = cart_z(LC, inu);
+        sfor<NB>([&](auto ilam_) {
+            constexpr int ilam = KX_CV(ilam_);
+            constexpr int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
+            const R* prow = P + (int64_t)(fb + ilam) * ldp + fd;
+            // T_{h'} = sum_sig E^{cd}_{nu sig,h'} P_{lam sig}
+            R Tv[nherm(LCD)];
+            sfor<LCD + 1>([&](auto t_) {
+                constexpr int t = KX_CV(t_);
+                sfor<LCD + 1 - t>([&](auto u_) {
+                    constexpr int u = KX_CV(u_);
+                    sfor<LCD + 1 - t - u>([&](auto v_) {
+                        constexpr int v = KX_CV(v_);
+                        if constexpr (reach(t, u, v, nx, ny, nz, LD)) Tv[hidx(t, u, v)] = R(0);
+                    });
+                });
+            });
+            sfor<ND>([&](auto isig_) {
+                constexpr int isig = KX_CV(isig_);
+                constexpr int sx = cart_x(LD, isig), sy = cart_y(LD, isig), sz = cart_z(LD, isig);
+                const R pv = __ldg(prow + isig);
+                sfor<nx + sx + 1>([&](auto t_) {
+                    constexpr int t = KX_CV(t_);
+                    sfor<ny + sy + 1>([&](auto u_) {
+                        constexpr int u = KX_CV(u_);
+                        const R exy = ecd[eidx(LC, LD, nx, sx, t)] * ecd[ECD + eidx(LC, LD, ny, sy, u)] * pv;
+                        sfor<nz + sz + 1>([&](auto v_) {
+                            constexpr int v = KX_CV(v_);
+                            Tv[hidx(t, u, v)] += exy * ecd[2 * ECD + eidx(LC, LD, nz, sz, v)];
+                        });
+                    });
+                });
+            });
+            // U_h = sum_{h'} (-1)^{|h'|} R_{h+h'} T_{h'}
+            R Uv[nherm(LAB)];
+            sfor<LAB + 1>([&](auto t_) {
+                constexpr int t = KX_CV(t_);
+                sfor<LAB + 1 - t>([&](auto u_) {
+                    constexpr int u = KX_CV(u_);
+                    sfor<LAB + 1 - t - u>([&](auto v_) {
+                        constexpr int v = KX_CV(v_);
+                        if constexpr (reach(t, u, v, lx, ly, lz, LA)) {
+                            R s = R(0);
+                            sfor<LCD + 1>([&](auto t2_) {
+                                constexpr int t2 = KX_CV(t2_);
+                                sfor<LCD + 1 - t2>([&](auto u2_) {
+                                    constexpr int u2 = KX_CV(u2_);
+                                    sfor<LCD + 1 - t2 - u2>([&](auto v2_) {
+                                        constexpr int v2 = KX_CV(v2_);
+                                        if constexpr (reach(t2, u2, v2, nx, ny, nz, LD)) {
+                                            if constexpr ((t2 + u2 + v2) & 1)
+                                                s -= Rt[hidx(t + t2, u + u2, v + v2)] * Tv[hidx(t2, u2, v2)];
+                                            else
+                                                s += Rt[hidx(t + t2, u + u2, v + v2)] * Tv[hidx(t2, u2, v2)];
+                                        }
+                                    });
+                                });
+                            });
+                            Uv[hidx(t, u, v)] = s;
+                        }
+                    });
+                });
+            });
+            // K_{mu nu} += sum_h E^{ab}_{mu lam,h} U_h
+            sfor<NA>([&](auto imu_) {
+                constexpr int imu = KX_CV(imu_);
+                constexpr int mx = cart_x(LA, imu), my = cart_y(LA, imu), mz = cart_z(LA, imu);
+                R s = R(0);
+                sfor<mx + lx + 1>([&](auto t_) {
+                    constexpr int t = KX_CV(t_);
+                    sfor<my + ly + 1>([&](auto u_) {
+                        constexpr int u = KX_CV(u_);
+                        const R exy = eab[eidx(LA, LB, mx, lx, t)] * eab[EAB + eidx(LA, LB, my, ly, u)];
+                        R sz_ = R(0);
+                        sfor<mz + lz + 1>([&](auto v_) {
+                            constexpr int v = KX_CV(v_);
+                            sz_ += eab[2 * EAB + eidx(LA, LB, mz, lz, v)] * Uv[hidx(t, u, v)];
+                        });
+                        s += exy * sz_;
+                    });
+                });
+                kacc[imu * NC + inu] += s;
+            });
+        });
+    });
+}
+
+// order B: loop mu in a, sig in d
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void contract_b(R* kacc, const R* Rt, const R* eab, const R* ecd,
+                                           const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD;
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    sfor<NA>([&](auto imu_) {
+        constexpr int imu = KX_CV(imu_);
+        constexpr int mx = cart_x(LA, imu), my = cart_y(LA, imu), mz = cart_z(LA, imu);
+        sfor<ND>([&](auto isig_) {
+            constexpr int isig = KX_CV(isig_);
+            constexpr int sx = cart_x(LD, isig), sy = cart_y(LD, isig), sz = cart_z(LD, isig);
+            // W_h = sum_lam E^{ab}_{mu lam,h} P_{lam sig}
+            R Wv[nherm(LAB)];
+            sfor<LAB + 1>([&](auto t_) {
+                constexpr int t = KX_CV(t_);
+                sfor<LAB + 1 - t>([&](auto u_) {
+                    constexpr int u = KX_CV(u_);
+                    sfor<LAB + 1 - t - u>([&](auto v_) {
+                        constexpr int v = KX_CV(v_);
+                        if constexpr (reach(t, u, v, mx, my, mz, LB)) Wv[hidx(t, u, v)] = R(0);
+                    });
+                });
+            });
+            sfor<NB>([&](auto ilam_) {
+                constexpr int ilam = KX_CV(ilam_);
+                constexpr int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
+                const R pv = __ldg(P + (int64_t)(fb + ilam) * ldp + fd + isig);
+                sfor<mx + lx + 1>([&](auto t_) {
+                    constexpr int t = KX_CV(t_);
+                    sfor<my + ly + 1>([&](auto u_) {
+                        constexpr int u = KX_CV(u_);
+                        const R exy = eab[eidx(LA, LB, mx, lx, t)] * eab[EAB + eidx(LA, LB, my, ly, u)] * pv;
+                        sfor<mz + lz + 1>([&](auto v_) {
+                            constexpr int v = KX_CV(v_);
+                            Wv[hidx(t, u, v)] += exy * eab[2 * EAB + eidx(LA, LB, mz, lz, v)];
+                        });
+                    });
+                });
+            });
+            // V_{h'} = sum_h R_{h+h'} W_h
+            R Vv[nherm(LCD)];
+            sfor<LCD + 1>([&](auto t2_) {
+                constexpr int t2 = KX_CV(t2_);
+                sfor<LCD + 1 - t2>([&](auto u2_) {
+                    constexpr int u2 = KX_CV(u2_);
+                    sfor<LCD + 1 - t2 - u2>([&](auto v2_) {
+                        constexpr int v2 = KX_CV(v2_);
+                        if constexpr (reach(t2, u2, v2, sx, sy, sz, LC)) {
+                            R s = R(0);
+                            sfor<LAB + 1>([&](auto t_) {
+                                constexpr int t = KX_CV(t_);
+                                sfor<LAB + 1 - t>([&](auto u_) {
+                                    constexpr int u = KX_CV(u_);
+                                    sfor<LAB + 1 - t - u>([&](auto v_) {
+                                        constexpr int v = KX_CV(v_);
+                                        if constexpr (reach(t, u, v, mx, my, mz, LB))
+                                            s += Rt[hidx(t + t2, u + u2, v + v2)] * Wv[hidx(t, u, v)];
+                                    });
+                                });
+                            });
+                            Vv[hidx(t2, u2, v2)] = s;
+                        }
+                    });
+                });
+            });
+            // K_{mu nu} += sum_{h'} (-1)^{|h'|} E^{cd}_{nu sig,h'} V_{h'}
+            sfor<NC>([&](auto inu_) {
+                constexpr int inu = KX_CV(inu_);
+                constexpr int nx = cart_x(LC, inu), ny = cart_y(LC, inu), nz = cart_z(LC, inu);
+                R s = R(0);
+                sfor<nx + sx + 1>([&](auto t_) {
+                    constexpr int t = KX_CV(t_);
+                    sfor<ny + sy + 1>([&](auto u_) {
+                        constexpr int u = KX_CV(u_);
+                        const R exy = ecd[eidx(LC, LD, nx, sx, t)] * ecd[ECD + eidx(LC, LD, ny, sy, u)];
+                        R sz_ = R(0);
+                        sfor<nz + sz + 1>([&](auto v_) {
+                            constexpr int v = KX_CV(v_);
+                            if constexpr ((t + u + v) & 1)
+                                sz_ -= ecd[2 * ECD + eidx(LC, LD, nz, sz, v)] * Vv[hidx(t, u, v)];
+                            else
+                                sz_ += ecd[2 * ECD + eidx(LC, LD, nz, sz, v)] * Vv[hidx(t, u, v)];
+                        });
+                        s += exy * sz_;
+                    });
+                });
+                kacc[imu * NC + inu] += s;
+            });
+        });
+    });
+}
+
+// ---------------------------------------------------------------------------
+// warp-level K reduction
+// ---------------------------------------------------------------------------
+
+// Sums the per-thread K partials over each run of lanes with the same
+// (fa, fc) and lets the last lane of the run add the sums into K (FP64).
+template <int NA, int NC, typename R>
+__device__ __forceinline__ void flush_k(R* kacc, int fa, int fc, double* __restrict__ K, int64_t ldk) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long key = fa < 0 ? -1ll : (((long long)fa << 32) | (unsigned)fc);
+    const long long prev = __shfl_up_sync(full, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(full, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+    sfor<NA * NC>([&](auto e_) {
+        constexpr int e = KX_CV(e_);
+        R v = kacc[e];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            R o = __shfl_up_sync(full, v, d);
+            if (lane - d >= start) v += o;
+        }
+        if (tail && key >= 0)
+            atomicAdd(K + (int64_t)(fa + e / NC) * ldk + fc + e % NC, to_f64(v));
+    });
+}
+
+// ---------------------------------------------------------------------------
+// the class kernel
+// ---------------------------------------------------------------------------
+
+constexpr int ERI_THREADS = 128;
+
+template <int LA, int LB, int LC, int LD, typename R>
+__global__ void __launch_bounds__(ERI_THREADS)
+k_eri(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra, const PairMeta* __restrict__ bmeta,
+      const R* __restrict__ ket, const PairMeta* __restrict__ kmeta, const R* __restrict__ boys,
+      const R* __restrict__ P, int64_t ldp, double* __restrict__ K, int64_t ldk, int64_t nab, int64_t ncd) {
+    constexpr int NA = ncart(LA), NC = ncart(LC);
+    constexpr int L = LA + LB + LC + LD;
+    constexpr int SAB = pair_stride(LA, LB), SCD = pair_stride(LC, LD);
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    const int64_t i = blockIdx.x * (int64_t)ERI_THREADS + threadIdx.x;
+    R kacc[NA * NC];
+    sfor<NA * NC>([&](auto e_) { kacc[KX_CV(e_)] = R(0); });
+    int fa = -1, fc = -1;
+    const Quartet q = i < n ? rec[i] : Quartet{-1, -1};
+    // slots outside the pair tables (never produced by the expansion) are skipped
+    if (q.ab >= 0 && q.ab < nab && q.cd >= 0 && q.cd < ncd) {
+        const R* pb = bra + (int64_t)q.ab * SAB;
+        const R* pk = ket + (int64_t)q.cd * SCD;
+        const PairMeta mb = bmeta[q.ab], mk = kmeta[q.cd];
+        fa = mb.fa;
+        fc = mk.fa;
+        R eab[3 * EAB], ecd[3 * ECD];
+        sfor<3 * EAB>([&](auto k_) { eab[KX_CV(k_)] = __ldg(pb + 5 + KX_CV(k_)); });
+        sfor<3 * ECD>([&](auto k_) { ecd[KX_CV(k_)] = __ldg(pk + 5 + KX_CV(k_)); });
+        const R p = __ldg(pb), qq = __ldg(pk);
+        const R X = __ldg(pb + 1) - __ldg(pk + 1);
+        const R Y = __ldg(pb + 2) - __ldg(pk + 2);
+        const R Z = __ldg(pb + 3) - __ldg(pk + 3);
+        const R pq = p * qq, sum = p + qq;
+        const R rho = pq / sum;
+        const R r2 = X * X + Y * Y + Z * Z;
+        const R T = rho * r2;
+        const R pref = R(2.0 * 17.493418327624862) * __ldg(pb + 4) * __ldg(pk + 4) / (pq * Real<R>::sqrt_(sum));
+        R G[L + 1];
+        boys_scaled<L, R>(G, T, rho, r2, pref, boys);
+        R Rt[nherm(L)];
+        hermite_r<L, R>(Rt, G, X, Y, Z);
+        if constexpr (use_order_a<LA, LB, LC, LD>())
+            contract_a<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
+        else
+            contract_b<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
+    }
+    flush_k<NA, NC, R>(kacc, fa, fc, K, ldk);
+}
+
+// ---------------------------------------------------------------------------
+// rolled variant for the large classes (L = la+lb+lc+ld >= ROLL_L)
+// ---------------------------------------------------------------------------
+//
+// The same arithmetic as k_eri, with the Cartesian and Hermite loops kept as
+// run-time loops and the intermediates in thread-local arrays.  Full
+// unrolling of these classes yields tens of thousands of straight-line
+// operations per thread, far past the register file; on GB300 the FP64
+// kernels are bound by the FP64 pipe, so the loop overhead is hidden there.
+
+constexpr int ROLL_L = 6;
+
+template <int L, typename R>
+__device__ __forceinline__ void hermite_r_rolled(R* Rt, const R* G, R X, R Y, R Z) {
+    Rt[0] = G[L];
+#pragma unroll 1
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll 1
+        for (int j = L - n; j >= 1; --j)
+#pragma unroll 1
+            for (int t = j; t >= 0; --t)
+#pragma unroll 1
+                for (int u = j - t; u >= 0; --u) {
+                    const int v = j - t - u;
+                    R r;
+                    if (t > 0) {
+                        r = X * Rt[hidx(t - 1, u, v)];
+                        if (t > 1) r += R(t - 1) * Rt[hidx(t - 2, u, v)];
+                    } else if (u > 0) {
+                        r = Y * Rt[hidx(t, u - 1, v)];
+                        if (u > 1) r += R(u - 1) * Rt[hidx(t, u - 2, v)];
+                    } else {
+                        r = Z * Rt[hidx(t, u, v - 1)];
+                        if (v > 1) r += R(v - 1) * Rt[hidx(t, u, v - 2)];
+                    }
+                    Rt[hidx(t, u, v)] = r;
+                }
+        Rt[0] = G[n];
+    }
+}
+
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void contract_a_rolled(R* kacc, const R* Rt, const R* eab, const R* ecd,
+                                                  const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD;
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+#pragma unroll 1
+    for (int inu = 0; inu < NC; ++inu) {
+        const int nx = cart_x(LC, inu), ny = cart_y(LC, inu), nz = cart_z(LC, inu);
+#pragma unroll 1
+        for (int ilam = 0; ilam < NB; ++ilam) {
+            const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
+            const R* prow = P + (int64_t)(fb + ilam) * ldp + fd;
+            R Tv[nherm(LCD)];
+#pragma unroll 1
+            for (int k = 0; k < nherm(LCD); ++k) Tv[k] = R(0);
+#pragma unroll 1
+            for (int isig = 0; isig < ND; ++isig) {
+                const int sx = cart_x(LD, isig), sy = cart_y(LD, isig), sz = cart_z(LD, isig);
+                const R pv = __ldg(prow + isig);
+#pragma unroll 1
+                for (int t = 0; t <= nx + sx; ++t)
+#pragma unroll 1
+                    for (int u = 0; u <= ny + sy; ++u) {
+                        const R exy = ecd[eidx(LC, LD, nx, sx, t)] * ecd[ECD + eidx(LC, LD, ny, sy, u)] * pv;
+#pragma unroll 1
+                        for (int v = 0; v <= nz + sz; ++v)
+                            Tv[hidx(t, u, v)] += exy * ecd[2 * ECD + eidx(LC, LD, nz, sz, v)];
+                    }
+            }
+            R Uv[nherm(LAB)];
+#pragma unroll 1
+            for (int t = 0; t <= LAB; ++t)
+#pragma unroll 1
+                for (int u = 0; t + u <= LAB; ++u)
+#pragma unroll 1
+                    for (int v = 0; t + u + v <= LAB; ++v) {
+                        if (!reach(t, u, v, lx, ly, lz, LA)) continue;
+                        R s = R(0);
+#pragma unroll 1
+                        for (int t2 = 0; t2 <= LCD; ++t2)
+#pragma unroll 1
+                            for (int u2 = 0; t2 + u2 <= LCD; ++u2)
+#pragma unroll 1
+                                for (int v2 = 0; t2 + u2 + v2 <= LCD; ++v2) {
+                                    if (!reach(t2, u2, v2, nx, ny, nz, LD)) continue;
+                                    const R term = Rt[hidx(t + t2, u + u2, v + v2)] * Tv[hidx(t2, u2, v2)];
+                                    s = ((t2 + u2 + v2) & 1) ? s - term : s + term;
+                                }
+                        Uv[hidx(t, u, v)] = s;
+                    }
+#pragma unroll 1
+            for (int imu = 0; imu < NA; ++imu) {
+                const int mx = cart_x(LA, imu), my = cart_y(LA, imu), mz = cart_z(LA, imu);
+                R s = R(0);
+#pragma unroll 1
+                for (int t = 0; t <= mx + lx; ++t)
+#pragma unroll 1
+                    for (int u = 0; u <= my + ly; ++u) {
+                        const R exy = eab[eidx(LA, LB, mx, lx, t)] * eab[EAB + eidx(LA, LB, my, ly, u)];
+                        R sz_ = R(0);
+#pragma unroll 1
+                        for (int v = 0; v <= mz + lz; ++v)
+                            sz_ += eab[2 * EAB + eidx(LA, LB, mz, lz, v)] * Uv[hidx(t, u, v)];
+                        s += exy * sz_;
+                    }
+                kacc[imu * NC + inu] += s;
+            }
+        }
+    }
+}
+
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void contract_b_rolled(R* kacc, const R* Rt, const R* eab, const R* ecd,
+                                                  const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD;
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+#pragma unroll 1
+    for (int imu = 0; imu < NA; ++imu) {
+        const int mx = cart_x(LA, imu), my = cart_y(LA, imu), mz = cart_z(LA, imu);
+#pragma unroll 1
+        for (int isig = 0; isig < ND; ++isig) {
+            const int sx = cart_x(LD, isig), sy = cart_y(LD, isig), sz = cart_z(LD, isig);
+            R Wv[nherm(LAB)];
+#pragma unroll 1
+            for (int k = 0; k < nherm(LAB); ++k) Wv[k] = R(0);
+#pragma unroll 1
+            for (int ilam = 0; ilam < NB; ++ilam) {
+                const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
+                const R pv = __ldg(P + (int64_t)(fb + ilam) * ldp + fd + isig);
+#pragma unroll 1
+                for (int t = 0; t <= mx + lx; ++t)
+#pragma unroll 1
+                    for (int u = 0; u <= my + ly; ++u) {
+                        const R exy = eab[eidx(LA, LB, mx, lx, t)] * eab[EAB + eidx(LA, LB, my, ly, u)] * pv;
+#pragma unroll 1
+                        for (int v = 0; v <= mz + lz; ++v)
+                            Wv[hidx(t, u, v)] += exy * eab[2 * EAB + eidx(LA, LB, mz, lz, v)];
+                    }
+            }
+            R Vv[nherm(LCD)];
+#pragma unroll 1
+            for (int t2 = 0; t2 <= LCD; ++t2)
+#pragma unroll 1
+                for (int u2 = 0; t2 + u2 <= LCD; ++u2)
+#pragma unroll 1
+                    for (int v2 = 0; t2 + u2 + v2 <= LCD; ++v2) {
+                        if (!reach(t2, u2, v2, sx, sy, sz, LC)) continue;
+                        R s = R(0);
+#pragma unroll 1
+                        for (int t = 0; t <= LAB; ++t)
+#pragma unroll 1
+                            for (int u = 0; t + u <= LAB; ++u)
+#pragma unroll 1
+                                for (int v = 0; t + u + v <= LAB; ++v)
+                                    if (reach(t, u, v, mx, my, mz, LB))
+                                        s += Rt[hidx(t + t2, u + u2, v + v2)] * Wv[hidx(t, u, v)];
+                        Vv[hidx(t2, u2, v2)] = s;
+                    }
+#pragma unroll 1
+            for (int inu = 0; inu < NC; ++inu) {
+                const int nx = cart_x(LC, inu), ny = cart_y(LC, inu), nz = cart_z(LC, inu);
+                R s = R(0);
+#pragma unroll 1
+                for (int t = 0; t <= nx + sx; ++t)
+#pragma unroll 1
+                    for (int u = 0; u <= ny + sy; ++u) {
+                        const R exy = ecd[eidx(LC, LD, nx, sx, t)] * ecd[ECD + eidx(LC, LD, ny, sy, u)];
+                        R sz_ = R(0);
+#pragma unroll 1
+                        for (int v = 0; v <= nz + sz; ++v) {
+                            const R term = ecd[2 * ECD + eidx(LC, LD, nz, sz, v)] * Vv[hidx(t, u, v)];
+                            sz_ = ((t + u + v) & 1) ? sz_ - term : sz_ + term;
+                        }
+                        s += exy * sz_;
+                    }
+                kacc[imu * NC + inu] += s;
+            }
+        }
+    }
+}
+
+template <int LA, int LB, int LC, int LD, typename R>
+__global__ void __launch_bounds__(ERI_THREADS)
+k_eri_rolled(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra,
+             const PairMeta* __restrict__ bmeta, const R* __restrict__ ket, const PairMeta* __restrict__ kmeta,
+             const R* __restrict__ boys, const R* __restrict__ P, int64_t ldp, double* __restrict__ K,
+             int64_t ldk, int64_t nab, int64_t ncd) {
+    constexpr int NA = ncart(LA), NC = ncart(LC);
+    constexpr int L = LA + LB + LC + LD;
+    constexpr int SAB = pair_stride(LA, LB), SCD = pair_stride(LC, LD);
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    const int64_t i = blockIdx.x * (int64_t)ERI_THREADS + threadIdx.x;
+    R kacc[NA * NC];
+#pragma unroll
+    for (int e = 0; e < NA * NC; ++e) kacc[e] = R(0);
+    int fa = -1, fc = -1;
+    const Quartet q = i < n ? rec[i] : Quartet{-1, -1};
+    // slots outside the pair tables (never produced by the expansion) are skipped
+    if (q.ab >= 0 && q.ab < nab && q.cd >= 0 && q.cd < ncd) {
+        const R* pb = bra + (int64_t)q.ab * SAB;
+        const R* pk = ket + (int64_t)q.cd * SCD;
+        const PairMeta mb = bmeta[q.ab], mk = kmeta[q.cd];
+        fa = mb.fa;
+        fc = mk.fa;
+        R eab[3 * EAB], ecd[3 * ECD];
+#pragma unroll 1
+        for (int k = 0; k < 3 * EAB; ++k) eab[k] = __ldg(pb + 5 + k);
+#pragma unroll 1
+        for (int k = 0; k < 3 * ECD; ++k) ecd[k] = __ldg(pk + 5 + k);
+        const R p = __ldg(pb), qq = __ldg(pk);
+        const R X = __ldg(pb + 1) - __ldg(pk + 1);
+        const R Y = __ldg(pb + 2) - __ldg(pk + 2);
+        const R Z = __ldg(pb + 3) - __ldg(pk + 3);
+        const R pq = p * qq, sum = p + qq;
+        const R rho = pq / sum;
+        const R r2 = X * X + Y * Y + Z * Z;
+        const R T = rho * r2;
+        const R pref = R(2.0 * 17.493418327624862) * __ldg(pb + 4) * __ldg(pk + 4) / (pq * Real<R>::sqrt_(sum));
+        R G[L + 1];
+        boys_scaled<L, R>(G, T, rho, r2, pref, boys);
+        R Rt[nherm(L)];
+        hermite_r_rolled<L, R>(Rt, G, X, Y, Z);
+        if constexpr (use_order_a<LA, LB, LC, LD>())
+            contract_a_rolled<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
+        else
+            contract_b_rolled<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
+    }
+    flush_k<NA, NC, R>(kacc, fa, fc, K, ldk);
+}
+
+// ---------------------------------------------------------------------------
+// algorithmic FLOP count of one quartet (mirrors the loops above)
+// ---------------------------------------------------------------------------
+
+template <int LA, int LB, int LC, int LD>
+double eri_flops() {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+    double f = 0;
+    f += 20;                                  // P-Q, rho, T, prefactor
+    f += 6 + (L + 1) * (2 * 6 + 1) + L;       // Boys (Taylor) and scaling
+    for (int n = L - 1; n >= 0; --n)          // Hermite recursion
+        for (int j = L - n; j >= 1; --j)
+            for (int t = j; t >= 0; --t)
+                for (int u = j - t; u >= 0; --u) {
+                    int v = j - t - u;
+                    int k = t > 0 ? t : (u > 0 ? u : v);
+                    f += (k > 1) ? 3 : 1;
+                }
+    auto nreach = [](int Lh, int x, int y, int z, int l2) {
+        int n = 0;
+        for (int t = 0; t <= Lh; ++t)
+            for (int u = 0; t + u <= Lh; ++u)
+                for (int v = 0; t + u + v <= Lh; ++v) n += reach(t, u, v, x, y, z, l2);
+        return n;
+    };
+    if (use_order_a<LA, LB, LC, LD>()) {
+        for (int nu = 0; nu < NC; ++nu)
+            for (int lam = 0; lam < NB; ++lam) {
+                int nx = cart_x(LC, nu), ny = cart_y(LC, nu), nz = cart_z(LC, nu);
+                int lx = cart_x(LB, lam), ly = cart_y(LB, lam), lz = cart_z(LB, lam);
+                for (int sig = 0; sig < ND; ++sig) {
+                    int sx = cart_x(LD, sig), sy = cart_y(LD, sig), sz = cart_z(LD, sig);
+                    f += (nx + sx + 1) * (ny + sy + 1) * (2 + 2 * (nz + sz + 1));
+                }
+                f += 2.0 * nreach(LAB, lx, ly, lz, LA) * nreach(LCD, nx, ny, nz, LD);
+                for (int mu = 0; mu < NA; ++mu) {
+                    int mx = cart_x(LA, mu), my = cart_y(LA, mu), mz = cart_z(LA, mu);
+                    f += (mx + lx + 1) * (my + ly + 1) * (3 + 2 * (mz + lz + 1)) + 1;
+                }
+            }
+    } else {
+        for (int mu = 0; mu < NA; ++mu)
+            for (int sig = 0; sig < ND; ++sig) {
+                int mx = cart_x(LA, mu), my = cart_y(LA, mu), mz = cart_z(LA, mu);
+                int sx = cart_x(LD, sig), sy = cart_y(LD, sig), sz = cart_z(LD, sig);
+                for (int lam = 0; lam < NB; ++lam) {
+                    int lx = cart_x(LB, lam), ly = cart_y(LB, lam), lz = cart_z(LB, lam);
+                    f += (mx + lx + 1) * (my + ly + 1) * (2 + 2 * (mz + lz + 1));
+                }
+                f += 2.0 * nreach(LAB, mx, my, mz, LB) * nreach(LCD, sx, sy, sz, LC);
+                for (int nu = 0; nu < NC; ++nu) {
+                    int nx = cart_x(LC, nu), ny = cart_y(LC, nu), nz = cart_z(LC, nu);
+                    f += (nx + sx + 1) * (ny + sy + 1) * (3 + 2 * (nz + sz + 1)) + 1;
+                }
+            }
+    }
+    return f;
+}
+
+template <int LA, int LB, int LC, int LD>
+int eri_launch_one(kx_ctx* c, int prec, const Quartet* rec, int64_t n, const double* P, int64_t ldp, double* K,
+                   int64_t ldk) {
+    constexpr int pab = LA * 3 + LB, pcd = LC * 3 + LD;
+    if (n <= 0) return KX_OK;
+    unsigned grid = (unsigned)((n + ERI_THREADS - 1) / ERI_THREADS);
+    if constexpr (LA + LB + LC + LD < ROLL_L) {
+        if (prec == 0)
+            k_eri<LA, LB, LC, LD, double><<<grid, ERI_THREADS, 0, c->stream>>>(
+                rec, n, c->d_pair64[pab], c->d_pairmeta[pab], c->d_pair64[pcd], c->d_pairmeta[pcd], c->d_boys64,
+                P, ldp, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
+        else
+            k_eri<LA, LB, LC, LD, float><<<grid, ERI_THREADS, 0, c->stream>>>(
+                rec, n, c->d_pair32[pab], c->d_pairmeta[pab], c->d_pair32[pcd], c->d_pairmeta[pcd], c->d_boys32,
+                c->d_P32, c->n_fn, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
+    } else {
+        if (prec == 0)
+            k_eri_rolled<LA, LB, LC, LD, double><<<grid, ERI_THREADS, 0, c->stream>>>(
+                rec, n, c->d_pair64[pab], c->d_pairmeta[pab], c->d_pair64[pcd], c->d_pairmeta[pcd], c->d_boys64,
+                P, ldp, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
+        else
+            k_eri_rolled<LA, LB, LC, LD, float><<<grid, ERI_THREADS, 0, c->stream>>>(
+                rec, n, c->d_pair32[pab], c->d_pairmeta[pab], c->d_pair32[pcd], c->d_pairmeta[pcd], c->d_boys32,
+                c->d_P32, c->n_fn, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
+    }
+    return KX_OK;
+}
+
+// dispatch over (lc, ld) for a fixed bra pair class (la, lb)
+#define KX_ERI_CASE(LA_, LB_, LC_, LD_) \
+    case LC_ * 3 + LD_: return eri_launch_one<LA_, LB_, LC_, LD_>(c, prec, rec, n, P, ldp, K, ldk);
+#define KX_ERI_DISPATCH(LA_, LB_)                                                                        \
+    int eri_launch_ab##LA_##LB_(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P, \
+                                int64_t ldp, double* K, int64_t ldk) {                                   \
+        switch (cls % 9) {                                                                               \
+            KX_ERI_CASE(LA_, LB_, 0, 0) KX_ERI_CASE(LA_, LB_, 0, 1) KX_ERI_CASE(LA_, LB_, 0, 2)          \
+            KX_ERI_CASE(LA_, LB_, 1, 0) KX_ERI_CASE(LA_, LB_, 1, 1) KX_ERI_CASE(LA_, LB_, 1, 2)          \
+            KX_ERI_CASE(LA_, LB_, 2, 0) KX_ERI_CASE(LA_, LB_, 2, 1) KX_ERI_CASE(LA_, LB_, 2, 2)          \
+            default: return KX_EINVAL;                                                                   \
+        }                                                                                                \
+    }                                                                                                    \
+    double class_flops_ab##LA_##LB_(int cls) {                                                           \
+        static const double f[9] = {eri_flops<LA_, LB_, 0, 0>(), eri_flops<LA_, LB_, 0, 1>(),             \
+                                    eri_flops<LA_, LB_, 0, 2>(), eri_flops<LA_, LB_, 1, 0>(),             \
+                                    eri_flops<LA_, LB_, 1, 1>(), eri_flops<LA_, LB_, 1, 2>(),             \
+                                    eri_flops<LA_, LB_, 2, 0>(), eri_flops<LA_, LB_, 2, 1>(),             \
+                                    eri_flops<LA_, LB_, 2, 2>()};                                         \
+        return f[cls % 9];                                                                               \
+    }
+
+}  // namespace kx

@@ -1,0 +1,211 @@
+// kx_expand.cu -- from surviving leaf quartets to shell-quartet records.
+//
+// A leaf quartet (A,B,C,D) holds |A||B||C||D| shell quartets.  With the
+// shell screen on, each is kept iff the metric query of Eq. 8 applied to the
+// single-shell blocks passes,
+//     beta = (S_ab * ||P_bd||_F) * S_cd > tau,
+// i.e. the recursion of Eq. 7 carried one level further, to single shells.
+// The test first runs on log2 values in FP32 (sum of three logs against
+// log2 tau); only quartets whose log sum lies within LOG_MARGIN of the
+// threshold -- a band wider than every FP32 rounding error in that sum --
+// are decided by the exact FP64 product.  The decision is therefore the
+// FP64 decision, at FP32 cost.  The same test against the split threshold
+// routes a kept quartet to the FP64 or the FP32 kernels in mixed mode.
+//
+// Records are binned by angular-momentum class and precision ("stream",
+// 162 of them).  One warp handles one leaf quartet; lanes walk its shell
+// quartets with d fastest, then b, c, a, so runs of equal (a,c) -- one K
+// block -- stay adjacent in each stream.  A first pass counts per stream, a
+// second writes through per-stream cursors with warp-aggregated atomics.
+#include <algorithm>
+#include <cmath>
+
+#include "kx_internal.cuh"
+
+namespace kx {
+
+constexpr float LOG_MARGIN = 1e-3f;   // log2 units; FP32 error of the sum < 6e-4
+
+struct ExpandArgs {
+    const Task* leaves;
+    int64_t n;
+    const int32_t* llo;
+    const int32_t* lhi;
+    const int32_t* tl;
+    int ns;
+    const float* slog;
+    const float* plog;
+    const double* snorm;
+    const double* pnorm;
+    const int32_t* pairmap;
+    double tau, split;
+    float ltau, lsplit;
+    int mixed, screen;
+};
+
+__device__ __forceinline__ bool above(float x, float lthr, double thr, const double* __restrict__ snorm,
+                                      const double* __restrict__ pnorm, int64_t ab, int64_t bd, int64_t cd) {
+    if (x > lthr + LOG_MARGIN) return true;
+    if (x < lthr - LOG_MARGIN) return false;
+    return __dmul_rn(__dmul_rn(snorm[ab], pnorm[bd]), snorm[cd]) > thr;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(256)
+k_expand(ExpandArgs p, unsigned long long* __restrict__ ctr, Quartet* __restrict__ rec,
+         unsigned long long* __restrict__ cand, const unsigned long long* __restrict__ end,
+         unsigned long long* __restrict__ err) {
+    __shared__ unsigned int scount[2 * NCLASS];
+    if (!WRITE) {
+        for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x) scount[i] = 0;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long ncand = 0;
+    for (int64_t q = warp; q < p.n; q += nwarp) {
+        const Task t = p.leaves[q];
+        const int a0 = p.llo[t.a], na = p.lhi[t.a] - a0;
+        const int b0 = p.llo[t.b], nb = p.lhi[t.b] - b0;
+        const int c0 = p.llo[t.c], nc = p.lhi[t.c] - c0;
+        const int d0 = p.llo[t.d], nd = p.lhi[t.d] - d0;
+        const int total = na * nb * nc * nd;
+        ncand += total;
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            int stream = -1;
+            int32_t pab = -1, pcd = -1;
+            if (idx < total) {
+                int r = idx;
+                const int id = r % nd; r /= nd;
+                const int ib = r % nb; r /= nb;
+                const int ic = r % nc;
+                const int ia = r / nc;
+                const int a = a0 + ia, b = b0 + ib, c = c0 + ic, d = d0 + id;
+                const int64_t ab = (int64_t)a * p.ns + b, bd = (int64_t)b * p.ns + d, cd = (int64_t)c * p.ns + d;
+                float x = 0.f;
+                if (p.screen || p.mixed) x = p.slog[ab] + p.plog[bd] + p.slog[cd];
+                bool keep = p.screen ? above(x, p.ltau, p.tau, p.snorm, p.pnorm, ab, bd, cd) : true;
+                if (keep) {
+                    pab = p.pairmap[ab];
+                    pcd = p.pairmap[cd];
+                    keep = pab >= 0 && pcd >= 0;
+                }
+                if (keep) {
+                    const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
+                    int prec = 0;
+                    if (p.mixed) prec = above(x, p.lsplit, p.split, p.snorm, p.pnorm, ab, bd, cd) ? 0 : 1;
+                    stream = prec * NCLASS + cls;
+                }
+            }
+            if (WRITE) {
+                const unsigned keepmask = __ballot_sync(0xffffffffu, stream >= 0);
+                if (stream >= 0) {
+                    const unsigned grp = __match_any_sync(keepmask, stream);
+                    const int leader = __ffs(grp) - 1;
+                    unsigned long long bas = 0;
+                    if (lane == leader) bas = atomicAdd(ctr + stream, (unsigned long long)__popc(grp));
+                    bas = __shfl_sync(grp, bas, leader);
+                    const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+                    // the count pass sized every stream; never write past it
+                    if (bas + rank < end[stream]) rec[bas + rank] = Quartet{pab, pcd};
+                    else atomicAdd(err, 1ull);
+                }
+            } else {
+                if (stream >= 0) atomicAdd(&scount[stream], 1u);
+            }
+        }
+    }
+    if (!WRITE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x)
+            if (scount[i]) atomicAdd(ctr + i, (unsigned long long)scount[i]);
+        for (int d = 16; d > 0; d >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, d);
+        if (lane == 0 && ncand) atomicAdd(cand, ncand / 32);
+    }
+}
+
+static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed,
+                            int screen) {
+    ExpandArgs a;
+    a.leaves = leaves;
+    a.n = n;
+    a.llo = c->d_leaf_lo;
+    a.lhi = c->d_leaf_hi;
+    a.tl = c->d_tl;
+    a.ns = c->n_shell;
+    a.slog = c->d_slog;
+    a.plog = c->d_plog;
+    a.snorm = c->d_snorm;
+    a.pnorm = c->d_pnorm;
+    a.pairmap = c->d_pairmap;
+    a.tau = tau;
+    a.split = split;
+    a.ltau = tau > 0.0 ? (float)std::log2(tau) : -INFINITY;
+    a.lsplit = split > 0.0 ? (float)std::log2(split) : -INFINITY;
+    a.mixed = mixed;
+    a.screen = screen;
+    return a;
+}
+
+static unsigned expand_grid(int64_t n) {
+    int64_t warps = n;
+    int64_t blocks = (warps + 7) / 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+}
+
+int expand_count(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed, int shell_screen,
+                 unsigned long long* d_count) {
+    if (n <= 0) return KX_OK;
+    ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
+    k_expand<false><<<expand_grid(n), 256, 0, c->stream>>>(a, d_count, nullptr, c->d_counters + CTR_CAND, nullptr,
+                                                            nullptr);
+    return KX_OK;
+}
+
+int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed, int shell_screen,
+                 unsigned long long* d_cursor, Quartet* rec) {
+    if (n <= 0) return KX_OK;
+    ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
+    k_expand<true><<<expand_grid(n), 256, 0, c->stream>>>(a, d_cursor, rec, nullptr, c->d_counters + CTR_END,
+                                                           c->d_counters + CTR_ERR);
+    return KX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// class dispatch
+// ---------------------------------------------------------------------------
+
+int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P, int64_t ldp,
+               double* K, int64_t ldk) {
+    switch (cls / 9) {
+        case 0: return eri_launch_ab00(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 1: return eri_launch_ab01(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 2: return eri_launch_ab02(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 3: return eri_launch_ab10(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 4: return eri_launch_ab11(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 5: return eri_launch_ab12(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 6: return eri_launch_ab20(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 7: return eri_launch_ab21(c, cls, prec, rec, n, P, ldp, K, ldk);
+        case 8: return eri_launch_ab22(c, cls, prec, rec, n, P, ldp, K, ldk);
+        default: return set_err(c, KX_EINVAL, "bad class");
+    }
+}
+
+double class_flops(int cls) {
+    switch (cls / 9) {
+        case 0: return class_flops_ab00(cls);
+        case 1: return class_flops_ab01(cls);
+        case 2: return class_flops_ab02(cls);
+        case 3: return class_flops_ab10(cls);
+        case 4: return class_flops_ab11(cls);
+        case 5: return class_flops_ab12(cls);
+        case 6: return class_flops_ab20(cls);
+        case 7: return class_flops_ab21(cls);
+        case 8: return class_flops_ab22(cls);
+        default: return 0.0;
+    }
+}
+
+}  // namespace kx

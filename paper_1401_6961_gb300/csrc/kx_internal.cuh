@@ -1,0 +1,293 @@
+// kx_internal.cuh -- internal types and device helpers of the exchange library.
+//
+// Index spaces used throughout:
+//   user shell      the order of kx_basis (P and K rows/columns follow it)
+//   tree position   Hilbert-ordered shells (atom-major, input order inside an
+//                   atom); the bisection tree of Eq. 1 is built over it
+//   level node      the nodes of traversal level k: a left-to-right partition
+//                   of the tree positions.  A leaf that stops splitting
+//                   before the deepest level is carried down unchanged (its
+//                   only child is itself), so every level partitions all
+//                   shells and level `depth` is the leaf partition.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kx.h"
+
+namespace kx {
+
+constexpr int LMAX = 2;
+constexpr int NCLASS = 81;          // (la,lb,lc,ld), l <= 2
+constexpr int NPAIRCLASS = 9;       // (la,lb)
+constexpr int MAX_LEVELS = 32;
+constexpr double PI = 3.14159265358979323846;
+// Boys table: F_m(T_i), T_i = i / BOYS_DENS for T < BOYS_TMAX, m = 0..BOYS_M
+// (orders up to 8 plus the 6 extra Taylor orders).
+constexpr int BOYS_M = 14;
+constexpr int BOYS_DENS = 32;
+constexpr double BOYS_TMAX = 40.0;
+constexpr int BOYS_NPTS = 40 * BOYS_DENS + 2;
+// layout of the small device counter array of a context
+constexpr int CTR_COUNT = 8;                       // per-stream record counts
+constexpr int CTR_CURSOR = CTR_COUNT + 2 * NCLASS; // per-stream write cursors
+constexpr int CTR_CAND = CTR_CURSOR + 2 * NCLASS;  // shell quartets screened
+constexpr int CTR_FILTER = CTR_CAND + 1;           // worklist export count
+constexpr int CTR_END = CTR_FILTER + 1;            // per-stream end offsets
+constexpr int CTR_ERR = CTR_END + 2 * NCLASS;      // write-guard violations
+constexpr int NCOUNTERS = 512;
+
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+// Hermite functions with t+u+v <= L
+__host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+// linear index of (t,u,v): block of total n = t+u+v, then s = u+v, then v
+__host__ __device__ constexpr int hidx(int t, int u, int v) {
+    return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+// Cartesian component k of angular momentum l (x power descending, then y)
+__host__ __device__ constexpr int cart_x(int l, int k) {
+    return l == 0 ? 0 : (l == 1 ? (k == 0 ? 1 : 0) : (k == 0 ? 2 : (k <= 2 ? 1 : 0)));
+}
+__host__ __device__ constexpr int cart_y(int l, int k) {
+    return l == 0 ? 0 : (l == 1 ? (k == 1 ? 1 : 0) : (k == 1 ? 1 : (k == 3 ? 2 : (k == 4 ? 1 : 0))));
+}
+__host__ __device__ constexpr int cart_z(int l, int k) { return l - cart_x(l, k) - cart_y(l, k); }
+
+// size of the per-dimension E table of a pair (la,lb): [i<=la][j<=lb][t<=la+lb]
+__host__ __device__ constexpr int etab(int la, int lb) { return (la + 1) * (lb + 1) * (la + lb + 1); }
+__host__ __device__ constexpr int eidx(int la, int lb, int i, int j, int t) {
+    return (i * (lb + 1) + j) * (la + lb + 1) + t;
+}
+// pair record: p, Px, Py, Pz, prefactor, Ex[], Ey[], Ez[] (padded to even)
+__host__ __device__ constexpr int pair_stride(int la, int lb) {
+    return ((5 + 3 * etab(la, lb)) + 1) & ~1;
+}
+
+// Shell pair metadata shared by the FP64 and FP32 pair tables.
+struct PairMeta {
+    int32_t fa, fb;   // user function offsets of the two shells
+    int32_t a, b;     // tree positions
+};
+
+// Shell quartet record: slots in the bra (la,lb) and ket (lc,ld) pair tables.
+struct Quartet {
+    int32_t ab, cd;
+};
+
+// A traversal task: node ids of level k (tree positions fit in 16 bits).
+struct Task {
+    uint16_t a, b, c, d;
+};
+
+struct LevelInfo {
+    int32_t n;        // nodes at this level
+    int32_t off;      // offset of the level in the flat node arrays
+};
+
+// Device-side view of a level's dense norm tables.
+struct NormLevel {
+    const double* s;  // ||Q_XY||_F, n x n
+    const double* p;  // ||P_XY||_F, n x n
+    int32_t n;
+};
+
+}  // namespace kx
+
+// ---------------------------------------------------------------------------
+// context (host side)
+// ---------------------------------------------------------------------------
+
+struct kx_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+
+    // basis (host copies)
+    int n_atom = 0, n_shell = 0;
+    int64_t n_fn = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> shell_atom, shell_l;
+    std::vector<double> shell_alpha;
+    std::vector<int64_t> fn_off;          // user shell -> first function
+
+    // order and tree
+    std::vector<int32_t> perm;            // tree position -> user shell
+    bool have_order = false, have_schwarz = false, have_tree = false;
+    int depth = 0;                        // deepest level
+    int leaf_max = 10;
+    std::vector<kx::LevelInfo> levels;    // 0..depth
+    std::vector<int32_t> node_lo, node_hi, node_child;   // flat over levels; child = first child
+    std::vector<int32_t> node_nchild;
+
+    // device: basis in tree order
+    int32_t* d_tl = nullptr;              // l by tree position
+    double* d_tctr = nullptr;             // centre [3] by tree position
+    double* d_talpha = nullptr;
+    int32_t* d_tfoff = nullptr;           // user function offset by tree position
+    int32_t* d_perm = nullptr;
+
+    // device: shell-pair tables in tree order (n_shell^2)
+    double* d_s2 = nullptr;               // squared Schwarz norms
+    double* d_snorm = nullptr;            // sqrt(s2)
+    float* d_slog = nullptr;              // log2(sqrt(s2)), -inf for 0
+    double* d_pq = nullptr;               // squared P shell-block norms (per build)
+    double* d_pnorm = nullptr;
+    float* d_plog = nullptr;
+
+    // device: tree + pyramids
+    int32_t* d_node_lo = nullptr;
+    int32_t* d_node_hi = nullptr;
+    int32_t* d_node_child = nullptr;
+    int32_t* d_node_nchild = nullptr;
+    std::vector<int64_t> pyr_off;         // offset of level k in the pyramid arrays
+    double* d_sq_s = nullptr;             // squared ||Q|| per level (dense)
+    double* d_sq_p = nullptr;
+    double* d_nrm_s = nullptr;            // sqrt of the above
+    double* d_nrm_p = nullptr;
+    int32_t* d_leaf_lo = nullptr;         // leaves (level depth) as tree ranges
+    int32_t* d_leaf_hi = nullptr;
+
+    // device: Boys table
+    double* d_boys64 = nullptr;
+    float* d_boys32 = nullptr;
+
+    // device: pair tables, rebuilt per build
+    int32_t* d_pairmap = nullptr;         // tree (a,b) -> slot in its class, -1 if absent
+    kx::PairMeta* d_pairmeta[kx::NPAIRCLASS] = {};
+    double* d_pair64[kx::NPAIRCLASS] = {};
+    float* d_pair32[kx::NPAIRCLASS] = {};
+    int64_t pair_cap[kx::NPAIRCLASS] = {};
+    int64_t n_pairs[kx::NPAIRCLASS] = {};
+
+    // device: scratch (grow-only)
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    kx::Task* d_front[2] = {nullptr, nullptr};
+    size_t front_cap[2] = {0, 0};
+    uint16_t* d_mask = nullptr;
+    size_t mask_cap = 0;
+    int64_t* d_scan = nullptr;
+    size_t scan_cap = 0;
+    kx::Quartet* d_rec = nullptr;
+    size_t rec_cap = 0;
+    unsigned long long* d_counters = nullptr;   // small device counters
+    kx::Task* d_keep = nullptr;                 // retained leaf worklist
+    size_t keep_cap = 0, keep_n = 0;
+    bool keep_valid = false;
+
+    // FP32 copy of P for the mixed-precision kernels (ld = n_fn)
+    float* d_P32 = nullptr;
+    size_t P32_cap = 0;
+    // scan temporaries
+    int64_t* d_scantmp = nullptr;
+    size_t scantmp_cap = 0;
+
+    // host-buffer entry point
+    double* d_hostP = nullptr;
+    double* d_hostK = nullptr;
+    size_t host_cap = 0;
+
+    double tau_ovlp = 0.0;
+    bool have_pq = false;
+    int64_t launches = 0;                 // kernels launched by the current build
+    // per-stream profile of the last profiled build
+    double prof_ms[2 * kx::NCLASS] = {};
+    int64_t prof_n[2 * kx::NCLASS] = {};
+    double prof_flops[2 * kx::NCLASS] = {};
+    int32_t prof_launches[2 * kx::NCLASS] = {};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+};
+
+namespace kx {
+
+// error helpers ---------------------------------------------------------------
+int set_err(kx_ctx* c, int code, const std::string& msg);
+int cuda_check(kx_ctx* c, cudaError_t e, const char* what);
+#define KX_CUDA(c, call)                                   \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return kx::cuda_check(c, _e, #call); \
+    } while (0)
+#define KX_TRY(call)                 \
+    do {                             \
+        int _r = (call);             \
+        if (_r != KX_OK) return _r;  \
+    } while (0)
+
+template <typename T>
+int grow(kx_ctx* c, T** p, size_t* cap, size_t need) {
+    if (need <= *cap && *p) return KX_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t n = need + need / 4 + 64;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, KX_ENOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    }
+    *cap = n;
+    return KX_OK;
+}
+
+// stage entry points (defined in the .cu files) ------------------------------
+int order_atoms(kx_ctx* c);                                  // kx_setup.cu
+int schwarz(kx_ctx* c, double tau_ovlp);                      // kx_setup.cu
+int build_tree(kx_ctx* c, int leaf_max);                      // kx_setup.cu
+int boys_table(kx_ctx* c);                                    // kx_setup.cu
+int p_norms(kx_ctx* c, const double* P, int64_t ldp);         // kx_setup.cu
+int pair_tables(kx_ctx* c, double tau, bool want32);          // kx_setup.cu
+int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);  // kx_traverse.cu
+int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
+                          double* K, int64_t ldk, kx_stats* st);  // kx_traverse.cu
+
+// shell expansion + class kernels (kx_expand.cu, kx_eri_*.cu)
+struct ClassCounts {
+    int64_t n[2 * NCLASS];     // [precision][class]; precision 0 = FP64
+};
+int expand_count(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
+                 int mixed, int shell_screen, unsigned long long* d_count);
+int expand_write(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
+                 int mixed, int shell_screen, unsigned long long* d_cursor, Quartet* rec);
+// launches the class kernel (la,lb,lc,ld) for n records; prec 0 = FP64, 1 = FP32
+// (prec 1 reads the FP32 copy of P, c->d_P32, leading dimension n_fn)
+int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+               int64_t ldp, double* K, int64_t ldk);
+int eri_launch_ab00(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab00(int cls);
+int eri_launch_ab01(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab01(int cls);
+int eri_launch_ab02(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab02(int cls);
+int eri_launch_ab10(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab10(int cls);
+int eri_launch_ab11(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab11(int cls);
+int eri_launch_ab12(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab12(int cls);
+int eri_launch_ab20(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab20(int cls);
+int eri_launch_ab21(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab21(int cls);
+int eri_launch_ab22(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
+                    int64_t ldp, double* K, int64_t ldk);
+double class_flops_ab22(int cls);
+
+// algorithmic FLOPs of one shell quartet of a class (the counter of the ERI kernels)
+double class_flops(int cls);
+int peak_probe(int device, int precision, double* gflops);   // kx_setup.cu
+
+}  // namespace kx

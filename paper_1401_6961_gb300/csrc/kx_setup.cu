@@ -1,0 +1,891 @@
+// kx_setup.cu -- geometry- and density-dependent set-up stages:
+//   * Hilbert ordering of the atoms (locality ordering, Sec. "Exchange as
+//     hextree traversal"),
+//   * ragged bisection of the shell index space (Eq. 1),
+//   * shell-pair Schwarz factors (the diagonal integrals of Eq. 8) with the
+//     optional overlap prune of Eq. 4,
+//   * the Frobenius-norm quadtrees (pyramids) of Eq. 2 for Q and P,
+//   * the Boys-function table and the per-pair Hermite expansion tables used
+//     by the McMurchie-Davidson kernels.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "kx_internal.cuh"
+
+namespace kx {
+
+int set_err(kx_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_check(kx_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return set_err(c, e == cudaErrorMemoryAllocation ? KX_ENOMEM : KX_ECUDA, m);
+}
+
+// ===========================================================================
+// Hilbert order
+// ===========================================================================
+
+// Key of a cell on a 2^bits grid per axis: Skilling's transpose form.  From
+// the top bit down, the low bits of every axis are either inverted (axis bit
+// set) or exchanged with axis 0 (bit clear); the axes are then Gray-coded
+// and the key is read by interleaving their bits, axis 0 most significant.
+__device__ uint64_t hilbert_key3(uint32_t x0, uint32_t x1, uint32_t x2, int bits) {
+    uint32_t X[3] = {x0, x1, x2};
+    for (uint32_t Q = 1u << (bits - 1); Q > 1; Q >>= 1) {
+        uint32_t low = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= low;
+            } else {
+                uint32_t t = (X[0] ^ X[i]) & low;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t flip = 0;
+    for (uint32_t Q = 1u << (bits - 1); Q > 1; Q >>= 1)
+        if (X[2] & Q) flip ^= Q - 1;
+    X[0] ^= flip;
+    X[1] ^= flip;
+    X[2] ^= flip;
+    uint64_t key = 0;
+    for (int b = bits - 1; b >= 0; --b)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> b) & 1u);
+    return key;
+}
+
+// One block: bounding box, keys, ranks of the atoms.
+__global__ void k_atom_keys(const double* __restrict__ xyz, int n, uint64_t* __restrict__ key,
+                           int32_t* __restrict__ rank) {
+    __shared__ double s_lo[3], s_hi[3];
+    if (threadIdx.x < 3) {
+        double lo = xyz[threadIdx.x], hi = xyz[threadIdx.x];
+        for (int a = 1; a < n; ++a) {
+            double v = xyz[3 * a + threadIdx.x];
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+        s_lo[threadIdx.x] = lo;
+        s_hi[threadIdx.x] = hi;
+    }
+    __syncthreads();
+    double span = 0.0;
+    for (int x = 0; x < 3; ++x) span = fmax(span, __dsub_rn(s_hi[x], s_lo[x]));
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        uint32_t q[3];
+        for (int x = 0; x < 3; ++x) {
+            int v = 0;
+            if (span > 0.0) {
+                // q = floor(((x - lo) / span) * 1023 + 0.5), each step rounded
+                double t = __ddiv_rn(__dsub_rn(xyz[3 * a + x], s_lo[x]), span);
+                double u = __dmul_rn(t, 1023.0);
+                v = (int)floor(__dadd_rn(u, 0.5));
+                v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
+            }
+            q[x] = (uint32_t)v;
+        }
+        key[a] = hilbert_key3(q[0], q[1], q[2], 10);
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        uint64_t ka = key[a];
+        int r = 0;
+        for (int b = 0; b < n; ++b) {
+            uint64_t kb = key[b];
+            r += (kb < ka) || (kb == ka && b < a);
+        }
+        rank[a] = r;
+    }
+}
+
+// Tree position of every shell: atoms by rank, input order inside an atom.
+__global__ void k_shell_pos(const int32_t* __restrict__ shell_atom, const int32_t* __restrict__ rank,
+                            int ns, int32_t* __restrict__ perm) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    int ra = rank[shell_atom[s]];
+    int pos = 0;
+    for (int t = 0; t < ns; ++t) {
+        int rt = rank[shell_atom[t]];
+        pos += (rt < ra) || (rt == ra && t < s);
+    }
+    perm[pos] = s;
+}
+
+int order_atoms(kx_ctx* c) {
+    int n = c->n_atom, ns = c->n_shell;
+    double* d_xyz = nullptr;
+    uint64_t* d_key = nullptr;
+    int32_t *d_rank = nullptr, *d_sa = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_xyz); cudaFree(d_key); cudaFree(d_rank); cudaFree(d_sa);
+    };
+    cudaError_t e = cudaMalloc(&d_xyz, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_key, sizeof(uint64_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_rank, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_sa, sizeof(int32_t) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_perm, sizeof(int32_t) * ns);
+    if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "order_atoms alloc"); }
+    cudaMemcpyAsync(d_xyz, c->xyz.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_sa, c->shell_atom.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream);
+    k_atom_keys<<<1, 1024, 0, c->stream>>>(d_xyz, n, d_key, d_rank);
+    k_shell_pos<<<(ns + 255) / 256, 256, 0, c->stream>>>(d_sa, d_rank, ns, c->d_perm);
+    c->perm.resize(ns);
+    cudaMemcpyAsync(c->perm.data(), c->d_perm, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) return cuda_check(c, e, "order_atoms");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "order_atoms kernels");
+    c->have_order = true;
+    return KX_OK;
+}
+
+// ===========================================================================
+// Hermite expansion coefficients (per dimension) and Hermite integrals
+// ===========================================================================
+
+// E^{ij}_t of the product of two 1D Gaussians with the Gaussian-product
+// factor left out: E^{00}_0 = 1,
+//   E^{i+1,j}_t = E^{ij}_{t-1}/(2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1},
+//   E^{i,j+1}_t = E^{ij}_{t-1}/(2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1}.
+// Output layout E[eidx(la,lb,i,j,t)].
+__device__ void hermite_e_1d(int la, int lb, double XPA, double XPB, double inv2p, double* E) {
+    const int LT = la + lb + 1;
+    #pragma unroll 1
+    for (int k = 0; k < etab(la, lb); ++k) E[k] = 0.0;
+    E[eidx(la, lb, 0, 0, 0)] = 1.0;
+    #pragma unroll 1
+    for (int i = 0; i <= la; ++i) {
+        if (i > 0) {
+            #pragma unroll 1
+            for (int t = 0; t <= i; ++t) {
+                double v = XPA * E[eidx(la, lb, i - 1, 0, t)];
+                if (t > 0) v += inv2p * E[eidx(la, lb, i - 1, 0, t - 1)];
+                if (t + 1 <= i - 1) v += (t + 1) * E[eidx(la, lb, i - 1, 0, t + 1)];
+                E[eidx(la, lb, i, 0, t)] = v;
+            }
+        }
+        #pragma unroll 1
+        for (int j = 1; j <= lb; ++j)
+            #pragma unroll 1
+            for (int t = 0; t <= i + j && t < LT; ++t) {
+                double v = XPB * E[eidx(la, lb, i, j - 1, t)];
+                if (t > 0) v += inv2p * E[eidx(la, lb, i, j - 1, t - 1)];
+                if (t + 1 <= i + j - 1) v += (t + 1) * E[eidx(la, lb, i, j - 1, t + 1)];
+                E[eidx(la, lb, i, j, t)] = v;
+            }
+    }
+}
+
+// Hermite Coulomb integrals R_{tuv} (n = 0) for t+u+v <= L at P-Q = (X,Y,Z),
+// from R^n_{000} = G_n (already scaled) by
+//   R^n_{t+1,u,v} = t R^{n+1}_{t-1,u,v} + X R^{n+1}_{t,u,v}  (same in u, v),
+// evaluated in place from the highest n down.  Generic L <= 8.
+__device__ void hermite_r_generic(int L, const double* G, double X, double Y, double Z, double* R) {
+    R[0] = G[L];
+    #pragma unroll 1
+    for (int n = L - 1; n >= 0; --n) {
+        #pragma unroll 1
+        for (int j = L - n; j >= 1; --j)
+            #pragma unroll 1
+            for (int t = j; t >= 0; --t)
+                #pragma unroll 1
+                for (int u = j - t; u >= 0; --u) {
+                    int v = j - t - u;
+                    double r;
+                    if (t > 0) {
+                        r = X * R[hidx(t - 1, u, v)];
+                        if (t > 1) r += (t - 1) * R[hidx(t - 2, u, v)];
+                    } else if (u > 0) {
+                        r = Y * R[hidx(t, u - 1, v)];
+                        if (u > 1) r += (u - 1) * R[hidx(t, u - 2, v)];
+                    } else {
+                        r = Z * R[hidx(t, u, v - 1)];
+                        if (v > 1) r += (v - 1) * R[hidx(t, u, v - 2)];
+                    }
+                    R[hidx(t, u, v)] = r;
+                }
+        R[0] = G[n];
+    }
+}
+
+__device__ double norm_prim(double a, int l) {
+    double df = (l == 2) ? 3.0 : 1.0;
+    return pow(2.0 * a / PI, 0.75) * pow(4.0 * a, 0.5 * l) / sqrt(df);
+}
+
+// ===========================================================================
+// Schwarz factors (Eq. 8) and the overlap prune (Eq. 4)
+// ===========================================================================
+
+// One thread per unordered pair a <= b (tree positions).  (ab|ab) has
+// P = Q, so T = 0, F_n(0) = 1/(2n+1), and R depends on rho = p/2 only.
+__global__ void k_schwarz(int ns, const int32_t* __restrict__ tl, const double* __restrict__ tctr,
+                          const double* __restrict__ talpha, double tau_ovlp,
+                          double* __restrict__ s2, double* __restrict__ snorm, float* __restrict__ slog) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t npair = (int64_t)ns * ns;
+    if (idx >= npair) return;
+    int a = (int)(idx / ns), b = (int)(idx % ns);
+    if (a > b) return;
+    int la = tl[a], lb = tl[b];
+    double A[3] = {tctr[3 * a], tctr[3 * a + 1], tctr[3 * a + 2]};
+    double B[3] = {tctr[3 * b], tctr[3 * b + 1], tctr[3 * b + 2]};
+    double al = talpha[a], be = talpha[b];
+    double p = al + be, inv2p = 0.5 / p;
+    double AB2 = 0.0;
+    double E[3][45];
+    #pragma unroll 1
+    for (int x = 0; x < 3; ++x) {
+        double Px = (al * A[x] + be * B[x]) / p;
+        AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+        hermite_e_1d(la, lb, Px - A[x], Px - B[x], inv2p, E[x]);
+    }
+    double Kab = exp(-al * be / p * AB2);
+    double na = norm_prim(al, la), nb = norm_prim(be, lb);
+    int pruned = 0;
+    if (tau_ovlp > 0.0) {
+        // (phi_mu, phi_nu) = N_a N_b K_ab (pi/p)^{3/2} E^x_0 E^y_0 E^z_0
+        double s0 = na * nb * Kab * pow(PI / p, 1.5);
+        double mx = 0.0;
+        #pragma unroll 1
+        for (int i = 0; i < ncart(la); ++i)
+            #pragma unroll 1
+            for (int j = 0; j < ncart(lb); ++j) {
+                double v = s0 * E[0][eidx(la, lb, cart_x(la, i), cart_x(lb, j), 0)] *
+                           E[1][eidx(la, lb, cart_y(la, i), cart_y(lb, j), 0)] *
+                           E[2][eidx(la, lb, cart_z(la, i), cart_z(lb, j), 0)];
+                mx = fmax(mx, fabs(v));
+            }
+        pruned = mx < tau_ovlp;
+    }
+    double total = 0.0;
+    if (!pruned) {
+        const int L = 2 * (la + lb);
+        double rho = 0.5 * p;
+        double pref = 2.0 * pow(PI, 2.5) / (p * p * sqrt(2.0 * p)) * Kab * Kab * na * na * nb * nb;
+        double G[9];
+        double s = pref;
+        #pragma unroll 1
+        for (int n = 0; n <= L; ++n) {
+            G[n] = s / (2 * n + 1);
+            s *= -2.0 * rho;
+        }
+        double R[165];
+        hermite_r_generic(L, G, 0.0, 0.0, 0.0, R);
+        // (mu lam|mu lam) = sum_{h,h'} E_h (-1)^{|h'|} E_h' R_{h+h'}
+        #pragma unroll 1
+        for (int i = 0; i < ncart(la); ++i)
+            #pragma unroll 1
+            for (int j = 0; j < ncart(lb); ++j) {
+                int ix = cart_x(la, i), iy = cart_y(la, i), iz = cart_z(la, i);
+                int jx = cart_x(lb, j), jy = cart_y(lb, j), jz = cart_z(lb, j);
+                double acc = 0.0;
+                #pragma unroll 1
+                for (int t = 0; t <= ix + jx; ++t)
+                    #pragma unroll 1
+                    for (int u = 0; u <= iy + jy; ++u)
+                        #pragma unroll 1
+                        for (int v = 0; v <= iz + jz; ++v) {
+                            double eh = E[0][eidx(la, lb, ix, jx, t)] * E[1][eidx(la, lb, iy, jy, u)] *
+                                        E[2][eidx(la, lb, iz, jz, v)];
+                            double inner = 0.0;
+                            #pragma unroll 1
+                            for (int t2 = 0; t2 <= ix + jx; ++t2)
+                                #pragma unroll 1
+                                for (int u2 = 0; u2 <= iy + jy; ++u2)
+                                    #pragma unroll 1
+                                    for (int v2 = 0; v2 <= iz + jz; ++v2) {
+                                        double e2 = E[0][eidx(la, lb, ix, jx, t2)] * E[1][eidx(la, lb, iy, jy, u2)] *
+                                                    E[2][eidx(la, lb, iz, jz, v2)];
+                                        double r = R[hidx(t + t2, u + u2, v + v2)];
+                                        inner += ((t2 + u2 + v2) & 1) ? -e2 * r : e2 * r;
+                                    }
+                            acc += eh * inner;
+                        }
+                total += acc;
+            }
+    }
+    double nrm = sqrt(total);
+    float lg = total > 0.0 ? (float)log2(nrm) : -INFINITY;
+    int64_t i1 = (int64_t)a * ns + b, i2 = (int64_t)b * ns + a;
+    s2[i1] = total; s2[i2] = total;
+    snorm[i1] = nrm; snorm[i2] = nrm;
+    slog[i1] = lg; slog[i2] = lg;
+}
+
+// basis in tree order
+__global__ void k_tree_basis(int ns, const int32_t* __restrict__ perm, const int32_t* __restrict__ l,
+                             const double* __restrict__ ctr, const double* __restrict__ alpha,
+                             const int32_t* __restrict__ foff, int32_t* __restrict__ tl,
+                             double* __restrict__ tctr, double* __restrict__ talpha,
+                             int32_t* __restrict__ tfoff) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    int s = perm[i];
+    tl[i] = l[s];
+    talpha[i] = alpha[s];
+    tfoff[i] = foff[s];
+    for (int x = 0; x < 3; ++x) tctr[3 * i + x] = ctr[3 * s + x];
+}
+
+int schwarz(kx_ctx* c, double tau_ovlp) {
+    int ns = c->n_shell;
+    int64_t n2 = (int64_t)ns * ns;
+    // upload the basis in user order, gather it into tree order
+    std::vector<double> ctr(3 * (size_t)ns);
+    std::vector<int32_t> foff(ns);
+    for (int s = 0; s < ns; ++s) {
+        for (int x = 0; x < 3; ++x) ctr[3 * s + x] = c->xyz[3 * c->shell_atom[s] + x];
+        foff[s] = (int32_t)c->fn_off[s];
+    }
+    int32_t *d_l = nullptr, *d_foff = nullptr;
+    double *d_ctr = nullptr, *d_alpha = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
+    if (!c->d_tl) {
+        A((void**)&c->d_tl, sizeof(int32_t) * ns);
+        A((void**)&c->d_tctr, sizeof(double) * 3 * ns);
+        A((void**)&c->d_talpha, sizeof(double) * ns);
+        A((void**)&c->d_tfoff, sizeof(int32_t) * ns);
+        A((void**)&c->d_s2, sizeof(double) * n2);
+        A((void**)&c->d_snorm, sizeof(double) * n2);
+        A((void**)&c->d_slog, sizeof(float) * n2);
+    }
+    A((void**)&d_l, sizeof(int32_t) * ns);
+    A((void**)&d_foff, sizeof(int32_t) * ns);
+    A((void**)&d_ctr, sizeof(double) * 3 * ns);
+    A((void**)&d_alpha, sizeof(double) * ns);
+    if (e != cudaSuccess) {
+        cudaFree(d_l); cudaFree(d_foff); cudaFree(d_ctr); cudaFree(d_alpha);
+        return cuda_check(c, e, "schwarz alloc");
+    }
+    cudaMemcpyAsync(d_l, c->shell_l.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_foff, foff.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_ctr, ctr.data(), sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_alpha, c->shell_alpha.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->stream);
+    k_tree_basis<<<(ns + 255) / 256, 256, 0, c->stream>>>(ns, c->d_perm, d_l, d_ctr, d_alpha, d_foff, c->d_tl,
+                                                          c->d_tctr, c->d_talpha, c->d_tfoff);
+    k_schwarz<<<(unsigned)((n2 + 127) / 128), 128, 0, c->stream>>>(ns, c->d_tl, c->d_tctr, c->d_talpha, tau_ovlp,
+                                                                 c->d_s2, c->d_snorm, c->d_slog);
+    e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_l); cudaFree(d_foff); cudaFree(d_ctr); cudaFree(d_alpha);
+    if (e != cudaSuccess) return cuda_check(c, e, "schwarz");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "schwarz kernels");
+    c->have_schwarz = true;
+    return KX_OK;
+}
+
+// ===========================================================================
+// ragged bisection (Eq. 1), one block, level by level
+// ===========================================================================
+
+constexpr int TREE_THREADS = 1024;
+
+// Block-wide exclusive scan of per-thread values (shared scratch of
+// TREE_THREADS ints); returns the exclusive prefix, *total gets the sum.
+__device__ int block_excl_scan(int v, int* sh, int* total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    int excl = x - v + (w > 0 ? sh[w - 1] : 0);
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Nodes of level k occupy [off_k, off_k + n_k) of the flat arrays.  A node
+// is a leaf when it holds at most leaf_max functions or a single shell; a
+// leaf is carried to the next level unchanged (one child).  A non-leaf is
+// split at the shell boundary s in (lo, hi) minimising
+// |2 pre[s] - pre[lo] - pre[hi]|, the lower s on a tie.
+__global__ void __launch_bounds__(TREE_THREADS)
+k_build_tree(int ns, const int32_t* __restrict__ tl, int leaf_max, int max_nodes, int32_t* __restrict__ pre,
+             int32_t* __restrict__ lo, int32_t* __restrict__ hi, int32_t* __restrict__ child,
+             int32_t* __restrict__ nchild, int32_t* __restrict__ level_n, int32_t* __restrict__ status) {
+    __shared__ int sh[32];
+    __shared__ int s_n, s_off, s_done;
+    // function-count prefix sums (sequential: ns <= 65535, once per geometry)
+    if (threadIdx.x == 0) {
+        pre[0] = 0;
+        for (int s = 0; s < ns; ++s) pre[s + 1] = pre[s] + ncart(tl[s]);
+        lo[0] = 0;
+        hi[0] = ns;
+        s_n = 1;
+        s_off = 0;
+        s_done = 0;
+        status[0] = 0;
+    }
+    __syncthreads();
+    int level = 0;
+    while (true) {
+        int n = s_n, off = s_off;
+        if (threadIdx.x == 0) level_n[level] = n;
+        // each thread handles a contiguous run of nodes
+        int per = (n + blockDim.x - 1) / blockDim.x;
+        int b0 = min(n, (int)threadIdx.x * per), b1 = min(n, b0 + per);
+        int mine = 0, nonleaf = 0;
+        for (int i = b0; i < b1; ++i) {
+            int l0 = lo[off + i], h0 = hi[off + i];
+            int leaf = (pre[h0] - pre[l0] <= leaf_max) || (h0 - l0 == 1);
+            nchild[off + i] = leaf ? 1 : 2;
+            mine += leaf ? 1 : 2;
+            nonleaf |= !leaf;
+        }
+        int total;
+        int base = block_excl_scan(mine, sh, &total);
+        int any = __syncthreads_or(nonleaf);
+        if (!any) break;                       // every node is a leaf: deepest level
+        if (off + n + total > max_nodes || level + 1 >= MAX_LEVELS) {
+            if (threadIdx.x == 0) status[0] = 1;
+            break;
+        }
+        int noff = off + n;
+        int pos = base;
+        for (int i = b0; i < b1; ++i) {
+            int l0 = lo[off + i], h0 = hi[off + i];
+            child[off + i] = pos;
+            if (nchild[off + i] == 1) {
+                lo[noff + pos] = l0;
+                hi[noff + pos] = h0;
+                pos += 1;
+            } else {
+                int target = pre[l0] + pre[h0];
+                // first s in (l0, h0) with 2 pre[s] >= target
+                int a = l0 + 1, b = h0 - 1, s1 = h0;
+                while (a <= b) {
+                    int m = (a + b) >> 1;
+                    if (2 * pre[m] >= target) { s1 = m; b = m - 1; } else { a = m + 1; }
+                }
+                int best;
+                if (s1 >= h0) best = h0 - 1;
+                else if (s1 - 1 > l0 && (target - 2 * pre[s1 - 1]) <= (2 * pre[s1] - target)) best = s1 - 1;
+                else best = s1;
+                lo[noff + pos] = l0;
+                hi[noff + pos] = best;
+                lo[noff + pos + 1] = best;
+                hi[noff + pos + 1] = h0;
+                pos += 2;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_off = noff;
+            s_n = total;
+        }
+        __syncthreads();
+        ++level;
+    }
+    if (threadIdx.x == 0) status[1] = level;
+}
+
+// ---------------------------------------------------------------------------
+// norm pyramids (Eq. 2): squared Frobenius norms per level, bottom-up
+// ---------------------------------------------------------------------------
+
+// deepest level: sum over the shells of the two leaves, a outer, b inner
+__global__ void k_pyr_leaves(int nl, int ns, const int32_t* __restrict__ llo, const int32_t* __restrict__ lhi,
+                             const double* __restrict__ sq_shell, double* __restrict__ sq,
+                             double* __restrict__ nrm) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nl * nl) return;
+    int X = (int)(i / nl), Y = (int)(i % nl);
+    double s = 0.0;
+    for (int a = llo[X]; a < lhi[X]; ++a)
+        for (int b = llo[Y]; b < lhi[Y]; ++b) s = __dadd_rn(s, sq_shell[(int64_t)a * ns + b]);
+    sq[i] = s;
+    nrm[i] = sqrt(s);
+}
+
+// level k from level k+1: children pairs in order (0,0),(0,1),(1,0),(1,1)
+__global__ void k_pyr_up(int n, int nn, const int32_t* __restrict__ child, const int32_t* __restrict__ nchild,
+                         const double* __restrict__ sq_next, double* __restrict__ sq, double* __restrict__ nrm) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * n) return;
+    int X = (int)(i / n), Y = (int)(i % n);
+    int cx = child[X], cy = child[Y], nx = nchild[X], ny = nchild[Y];
+    double s = 0.0;
+    for (int ii = 0; ii < nx; ++ii)
+        for (int jj = 0; jj < ny; ++jj) s = __dadd_rn(s, sq_next[(int64_t)(cx + ii) * nn + (cy + jj)]);
+    sq[i] = s;
+    nrm[i] = sqrt(s);
+}
+
+static int build_pyramid(kx_ctx* c, const double* sq_shell, double* sq, double* nrm) {
+    int D = c->depth;
+    int nl = c->levels[D].n;
+    int64_t n2 = (int64_t)nl * nl;
+    k_pyr_leaves<<<(unsigned)((n2 + 255) / 256), 256, 0, c->stream>>>(nl, c->n_shell, c->d_leaf_lo, c->d_leaf_hi,
+                                                                    sq_shell, sq + c->pyr_off[D], nrm + c->pyr_off[D]);
+    c->launches += 1 + D;
+    for (int k = D - 1; k >= 0; --k) {
+        int n = c->levels[k].n, nn = c->levels[k + 1].n;
+        int64_t m = (int64_t)n * n;
+        k_pyr_up<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(
+            n, nn, c->d_node_child + c->levels[k].off, c->d_node_nchild + c->levels[k].off,
+            sq + c->pyr_off[k + 1], sq + c->pyr_off[k], nrm + c->pyr_off[k]);
+    }
+    return KX_OK;
+}
+
+int build_tree(kx_ctx* c, int leaf_max) {
+    int ns = c->n_shell;
+    int max_nodes = MAX_LEVELS * ns + 1;
+    int32_t *d_pre = nullptr, *d_lo = nullptr, *d_hi = nullptr, *d_child = nullptr, *d_nchild = nullptr,
+            *d_leveln = nullptr, *d_status = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](int32_t** p, size_t n) { if (e == cudaSuccess) e = cudaMalloc(p, sizeof(int32_t) * n); };
+    A(&d_pre, ns + 1); A(&d_lo, max_nodes); A(&d_hi, max_nodes); A(&d_child, max_nodes);
+    A(&d_nchild, max_nodes); A(&d_leveln, MAX_LEVELS); A(&d_status, 2);
+    auto cleanup = [&]() {
+        cudaFree(d_pre); cudaFree(d_lo); cudaFree(d_hi); cudaFree(d_child); cudaFree(d_nchild);
+        cudaFree(d_leveln); cudaFree(d_status);
+    };
+    if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "build_tree alloc"); }
+    k_build_tree<<<1, TREE_THREADS, 0, c->stream>>>(ns, c->d_tl, leaf_max, max_nodes, d_pre, d_lo, d_hi, d_child,
+                                                    d_nchild, d_leveln, d_status);
+    int32_t status[2] = {0, 0};
+    std::vector<int32_t> leveln(MAX_LEVELS, 0);
+    cudaMemcpyAsync(status, d_status, sizeof(status), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(leveln.data(), d_leveln, sizeof(int32_t) * MAX_LEVELS, cudaMemcpyDeviceToHost, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "build_tree"); }
+    if (status[0] != 0) {
+        cleanup();
+        return set_err(c, KX_ECAPACITY, "bisection deeper than the supported 32 levels");
+    }
+    int D = status[1];
+    c->depth = D;
+    c->leaf_max = leaf_max;
+    c->levels.assign(D + 1, LevelInfo{0, 0});
+    int off = 0;
+    for (int k = 0; k <= D; ++k) {
+        c->levels[k].n = leveln[k];
+        c->levels[k].off = off;
+        off += leveln[k];
+    }
+    int total = off;
+    c->node_lo.resize(total); c->node_hi.resize(total); c->node_child.resize(total); c->node_nchild.resize(total);
+    cudaMemcpy(c->node_lo.data(), d_lo, sizeof(int32_t) * total, cudaMemcpyDeviceToHost);
+    cudaMemcpy(c->node_hi.data(), d_hi, sizeof(int32_t) * total, cudaMemcpyDeviceToHost);
+    cudaMemcpy(c->node_child.data(), d_child, sizeof(int32_t) * total, cudaMemcpyDeviceToHost);
+    cudaMemcpy(c->node_nchild.data(), d_nchild, sizeof(int32_t) * total, cudaMemcpyDeviceToHost);
+    cleanup();
+    // keep compact device copies
+    cudaFree(c->d_node_lo); cudaFree(c->d_node_hi); cudaFree(c->d_node_child); cudaFree(c->d_node_nchild);
+    cudaFree(c->d_leaf_lo); cudaFree(c->d_leaf_hi);
+    c->d_node_lo = c->d_node_hi = c->d_node_child = c->d_node_nchild = c->d_leaf_lo = c->d_leaf_hi = nullptr;
+    int nl = c->levels[D].n;
+    e = cudaSuccess;
+    A(&c->d_node_lo, total); A(&c->d_node_hi, total); A(&c->d_node_child, total); A(&c->d_node_nchild, total);
+    A(&c->d_leaf_lo, nl); A(&c->d_leaf_hi, nl);
+    if (e != cudaSuccess) return cuda_check(c, e, "build_tree alloc");
+    cudaMemcpyAsync(c->d_node_lo, c->node_lo.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_node_hi, c->node_hi.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_node_child, c->node_child.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_node_nchild, c->node_nchild.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice,
+                    c->stream);
+    cudaMemcpyAsync(c->d_leaf_lo, c->node_lo.data() + c->levels[D].off, sizeof(int32_t) * nl, cudaMemcpyHostToDevice,
+                    c->stream);
+    cudaMemcpyAsync(c->d_leaf_hi, c->node_hi.data() + c->levels[D].off, sizeof(int32_t) * nl, cudaMemcpyHostToDevice,
+                    c->stream);
+    // pyramid storage
+    c->pyr_off.assign(D + 2, 0);
+    for (int k = 0; k <= D; ++k) c->pyr_off[k + 1] = c->pyr_off[k] + (int64_t)c->levels[k].n * c->levels[k].n;
+    int64_t pyr = c->pyr_off[D + 1];
+    cudaFree(c->d_sq_s); cudaFree(c->d_sq_p); cudaFree(c->d_nrm_s); cudaFree(c->d_nrm_p);
+    c->d_sq_s = c->d_sq_p = c->d_nrm_s = c->d_nrm_p = nullptr;
+    auto AD = [&](double** p) { if (e == cudaSuccess) e = cudaMalloc(p, sizeof(double) * pyr); };
+    AD(&c->d_sq_s); AD(&c->d_sq_p); AD(&c->d_nrm_s); AD(&c->d_nrm_p);
+    if (e != cudaSuccess) return cuda_check(c, e, "pyramid alloc");
+    KX_TRY(build_pyramid(c, c->d_s2, c->d_sq_s, c->d_nrm_s));
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "schwarz pyramid");
+    c->have_tree = true;
+    c->have_pq = false;
+    return KX_OK;
+}
+
+// ===========================================================================
+// P shell-block norms and their pyramid
+// ===========================================================================
+
+__global__ void k_p_shell(int ns, const int32_t* __restrict__ tl, const int32_t* __restrict__ tfoff,
+                          const double* __restrict__ P, int64_t ldp, double* __restrict__ pq,
+                          double* __restrict__ pn, float* __restrict__ plog) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ns * ns) return;
+    int b = (int)(i / ns), d = (int)(i % ns);
+    int fb = tfoff[b], fd = tfoff[d], nb = ncart(tl[b]), nd = ncart(tl[d]);
+    double s = 0.0;
+    for (int x = 0; x < nb; ++x)
+        for (int y = 0; y < nd; ++y) {
+            double v = P[(int64_t)(fb + x) * ldp + fd + y];
+            s = __dadd_rn(s, __dmul_rn(v, v));
+        }
+    pq[i] = s;
+    double r = sqrt(s);
+    pn[i] = r;
+    plog[i] = s > 0.0 ? (float)log2(r) : -INFINITY;
+}
+
+int p_norms(kx_ctx* c, const double* P, int64_t ldp) {
+    int ns = c->n_shell;
+    int64_t n2 = (int64_t)ns * ns;
+    cudaError_t e = cudaSuccess;
+    if (!c->d_pq) {
+        e = cudaMalloc(&c->d_pq, sizeof(double) * n2);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_pnorm, sizeof(double) * n2);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_plog, sizeof(float) * n2);
+        if (e != cudaSuccess) return cuda_check(c, e, "p_norms alloc");
+    }
+    k_p_shell<<<(unsigned)((n2 + 255) / 256), 256, 0, c->stream>>>(ns, c->d_tl, c->d_tfoff, P, ldp, c->d_pq,
+                                                                  c->d_pnorm, c->d_plog);
+    c->launches++;
+    KX_TRY(build_pyramid(c, c->d_pq, c->d_sq_p, c->d_nrm_p));
+    c->have_pq = true;
+    return KX_OK;
+}
+
+// ===========================================================================
+// Boys table
+// ===========================================================================
+
+// F_m(T_i), T_i = i / BOYS_DENS, m = 0..BOYS_M: the top order from its
+// positive-term series e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)),
+// the rest by downward recursion F_{m-1} = (2T F_m + e^{-T}) / (2m-1).
+__global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32, int npts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npts) return;
+    double T = (double)i / BOYS_DENS;
+    const int M = BOYS_M;
+    double term = 1.0 / (2 * M + 1), sum = term;
+    #pragma unroll 1
+    for (int k = 1; k < 4000; ++k) {
+        term *= 2.0 * T / (2 * M + 2 * k + 1);
+        sum += term;
+        if (term < 1e-19 * sum) break;
+    }
+    double e = exp(-T);
+    double F[BOYS_M + 1];
+    F[M] = e * sum;
+    #pragma unroll 1
+    for (int m = M; m > 0; --m) F[m - 1] = (2.0 * T * F[m] + e) / (2 * m - 1);
+    #pragma unroll 1
+    for (int m = 0; m <= M; ++m) {
+        t64[(int64_t)i * (BOYS_M + 1) + m] = F[m];
+        t32[(int64_t)i * (BOYS_M + 1) + m] = (float)F[m];
+    }
+}
+
+int boys_table(kx_ctx* c) {
+    int npts = BOYS_NPTS;
+    cudaError_t e = cudaMalloc(&c->d_boys64, sizeof(double) * npts * (BOYS_M + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_boys32, sizeof(float) * npts * (BOYS_M + 1));
+    if (e != cudaSuccess) return cuda_check(c, e, "boys alloc");
+    k_boys_table<<<(npts + 127) / 128, 128, 0, c->stream>>>(c->d_boys64, c->d_boys32, npts);
+    return KX_OK;
+}
+
+// ===========================================================================
+// pair tables for the ERI kernels
+// ===========================================================================
+
+// significant(a,b): the pair can appear in a surviving shell quartet.  With
+// the shell screen on, (S_ab * Pmax) * Smax <= tau implies every quartet
+// through (a,b) is culled (products of non-negative doubles are monotone).
+// Pairs emptied by Eq. 4 (s2 = 0) never take part.
+__global__ void k_pair_flags(int ns, const int32_t* __restrict__ tl, const double* __restrict__ snorm,
+                             const double* __restrict__ s2, double tau, double pmax, double smax, int screen,
+                             int cls, int64_t* __restrict__ flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ns * ns) return;
+    int a = (int)(i / ns), b = (int)(i % ns);
+    int ok = (tl[a] * 3 + tl[b] == cls) && s2[i] > 0.0;
+    if (ok && screen) ok = __dmul_rn(__dmul_rn(snorm[i], pmax), smax) > tau;
+    flag[i] = ok;
+}
+
+__global__ void k_pair_fill(int ns, int cls, const int32_t* __restrict__ tl, const double* __restrict__ tctr,
+                            const double* __restrict__ talpha, const int32_t* __restrict__ tfoff,
+                            const int64_t* __restrict__ flag, const int64_t* __restrict__ slot,
+                            int32_t* __restrict__ pairmap, PairMeta* __restrict__ meta,
+                            double* __restrict__ d64, float* __restrict__ d32) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ns * ns) return;
+    int a = (int)(i / ns), b = (int)(i % ns);
+    if (tl[a] * 3 + tl[b] != cls) return;
+    if (!flag[i]) {
+        pairmap[i] = -1;
+        return;
+    }
+    int64_t s = slot[i];
+    pairmap[i] = (int32_t)s;
+    int la = tl[a], lb = tl[b];
+    meta[s] = PairMeta{tfoff[a], tfoff[b], a, b};
+    double al = talpha[a], be = talpha[b], p = al + be;
+    double A[3] = {tctr[3 * a], tctr[3 * a + 1], tctr[3 * a + 2]};
+    double B[3] = {tctr[3 * b], tctr[3 * b + 1], tctr[3 * b + 2]};
+    const int stride = pair_stride(la, lb), et = etab(la, lb);
+    double* o = d64 + s * stride;
+    float* o32 = d32 + s * stride;
+    double AB2 = 0.0;
+    double E[45];
+    o[0] = p;
+    for (int x = 0; x < 3; ++x) {
+        double Px = (al * A[x] + be * B[x]) / p;
+        o[1 + x] = Px;
+        AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+        hermite_e_1d(la, lb, Px - A[x], Px - B[x], 0.5 / p, E);
+        for (int k = 0; k < et; ++k) o[5 + x * et + k] = E[k];
+    }
+    o[4] = norm_prim(al, la) * norm_prim(be, lb) * exp(-al * be / p * AB2);
+    if (stride > 5 + 3 * et) o[stride - 1] = 0.0;
+    for (int k = 0; k < stride; ++k) o32[k] = (float)o[k];
+}
+
+__global__ void k_max_reduce(const double* __restrict__ x, int64_t n, unsigned long long* __restrict__ out) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, x[i]);
+    for (int d = 16; d > 0; d >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+int pair_tables(kx_ctx* c, double tau, bool screen) {
+    int ns = c->n_shell;
+    int64_t n2 = (int64_t)ns * ns;
+    // maxima of S and of the P shell-block norms
+    unsigned long long* d_mx = c->d_counters;   // two slots
+    cudaMemsetAsync(d_mx, 0, 2 * sizeof(unsigned long long), c->stream);
+    k_max_reduce<<<1024, 256, 0, c->stream>>>(c->d_snorm, n2, d_mx);
+    k_max_reduce<<<1024, 256, 0, c->stream>>>(c->d_pnorm, n2, d_mx + 1);
+    c->launches += 2;
+    unsigned long long mx[2];
+    cudaMemcpyAsync(mx, d_mx, sizeof(mx), cudaMemcpyDeviceToHost, c->stream);
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    double smax, pmax;
+    memcpy(&smax, &mx[0], 8);
+    memcpy(&pmax, &mx[1], 8);
+    if (!c->d_pairmap) KX_CUDA(c, cudaMalloc(&c->d_pairmap, sizeof(int32_t) * n2));
+    KX_TRY(grow(c, &c->d_scan, &c->scan_cap, (size_t)2 * n2 + 16));
+    int64_t* flag = c->d_scan;
+    int64_t* slot = c->d_scan + n2;
+    unsigned g = (unsigned)((n2 + 255) / 256);
+    for (int cls = 0; cls < NPAIRCLASS; ++cls) {
+        int la = cls / 3, lb = cls % 3;
+        k_pair_flags<<<g, 256, 0, c->stream>>>(ns, c->d_tl, c->d_snorm, c->d_s2, tau, pmax, smax, screen ? 1 : 0,
+                                               cls, flag);
+        int64_t total = 0;
+        KX_TRY(exclusive_scan(c, flag, slot, n2, &total));
+        c->n_pairs[cls] = total;
+        size_t need = (size_t)std::max<int64_t>(total, 1);
+        if ((size_t)c->pair_cap[cls] < need) {
+            cudaFree(c->d_pair64[cls]); cudaFree(c->d_pair32[cls]); cudaFree(c->d_pairmeta[cls]);
+            c->d_pair64[cls] = nullptr; c->d_pair32[cls] = nullptr; c->d_pairmeta[cls] = nullptr;
+            size_t cap = need + need / 8 + 16;
+            int stride = pair_stride(la, lb);
+            cudaError_t e = cudaMalloc(&c->d_pair64[cls], sizeof(double) * stride * cap);
+            if (e == cudaSuccess) e = cudaMalloc(&c->d_pair32[cls], sizeof(float) * stride * cap);
+            if (e == cudaSuccess) e = cudaMalloc(&c->d_pairmeta[cls], sizeof(PairMeta) * cap);
+            if (e != cudaSuccess) {
+                c->pair_cap[cls] = 0;
+                return cuda_check(c, e, "pair table alloc");
+            }
+            c->pair_cap[cls] = (int64_t)cap;
+        }
+        k_pair_fill<<<g, 256, 0, c->stream>>>(ns, cls, c->d_tl, c->d_tctr, c->d_talpha, c->d_tfoff, flag, slot,
+                                              c->d_pairmap, c->d_pairmeta[cls], c->d_pair64[cls], c->d_pair32[cls]);
+        c->launches += 2;
+    }
+    return KX_OK;
+}
+
+// ===========================================================================
+// FMA throughput probe
+// ===========================================================================
+
+// Eight independent multiply-add chains per thread; x <- x*a + b converges
+// to b/(1-a), so the values stay finite for any iteration count.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fma_probe(R* __restrict__ out, int iters, R a, R b) {
+    R x0 = R(threadIdx.x) * R(1e-3), x1 = x0 + R(1), x2 = x0 + R(2), x3 = x0 + R(3);
+    R x4 = x0 + R(4), x5 = x0 + R(5), x6 = x0 + R(6), x7 = x0 + R(7);
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+        x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+        x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+int peak_probe(int device, int precision, double* gflops) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return KX_ECUDA;
+    }
+    const int blocks = prop.multiProcessorCount * 8, threads = 256;
+    const int iters = precision == KX_FP64 ? 1 << 12 : 1 << 17;
+    void* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return KX_ENOMEM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int rep = 0; rep < 6; ++rep) {
+        cudaEventRecord(e0);
+        if (precision == KX_FP64)
+            k_fma_probe<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-6);
+        else
+            k_fma_probe<float><<<blocks, threads>>>((float*)out, iters, 0.9999f, 1e-4f);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+        if (rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e9);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return KX_ECUDA;
+    *gflops = best;
+    return KX_OK;
+}
+
+}  // namespace kx

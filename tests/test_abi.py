@@ -1,0 +1,85 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point
+declared in include/kx.h, and rejects bad calls before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1401_6961_gb300 import build
+    build.build()
+    import paper_1401_6961_gb300 as kx
+    return kx.load()
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "kx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kx_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for n in ("kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange", "kx_exchange_host",
+              "kx_get_worklist", "kx_get_norms", "kx_last_error", "kx_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_1401_6961_gb300 as kx
+    names = declared_entry_points()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(kx.EXPORTS) == names
+
+
+def test_default_opts(lib):
+    import paper_1401_6961_gb300 as kx
+    o = kx.kx_default_opts()
+    assert o.tau == 1e-10 and o.precision == kx.KX_FP64 and o.shell_screen == 1
+    assert o.keep_worklist == 0 and o.chunk_records == 0
+
+
+def test_struct_layouts_match_header(lib):
+    import paper_1401_6961_gb300 as kx
+    assert ctypes.sizeof(kx.kx_opts) == 40
+    assert ctypes.sizeof(kx.kx_basis) == 40
+    # 4 counters + 32 levels + 4 ints + 8 doubles
+    assert ctypes.sizeof(kx.kx_stats) == 8 * 4 + 8 * 32 + 4 * 4 + 8 * 8
+
+
+def test_create_rejects_bad_basis_without_gpu(lib):
+    import paper_1401_6961_gb300 as kx
+    xyz = np.zeros((1, 3))
+    good = dict(xyz=xyz, shell_atom=[0], shell_l=[0], shell_alpha=[1.0])
+    bad = [dict(good, shell_l=[3]), dict(good, shell_alpha=[-1.0]), dict(good, shell_atom=[1]),
+           dict(good, shell_alpha=[float("nan")]), dict(good, xyz=np.array([[np.inf, 0, 0]]))]
+    for b in bad:
+        with pytest.raises(kx.KxError) as e:
+            kx.kx_create(**b)
+        assert e.value.code == kx.KX_EINVAL
+
+
+def test_null_context_calls(lib):
+    import paper_1401_6961_gb300 as kx
+    assert lib.kx_build_schwarz(None, 0.0) == kx.KX_EINVAL
+    assert lib.kx_build_tree(None, 10, None) == kx.KX_EINVAL
+    assert lib.kx_n_functions(None) == -1
+    assert lib.kx_last_error(None) == b"null context"
+    lib.kx_destroy(None)
+
+
+def test_no_gpu_reports_cuda_error(lib):
+    import torch
+    import paper_1401_6961_gb300 as kx
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(kx.KxError) as e:
+        kx.kx_create(np.zeros((1, 3)), [0], [0], [1.0])
+    assert e.value.code == kx.KX_ECUDA
