@@ -501,7 +501,7 @@ k_eri(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra, con
 }
 
 // ---------------------------------------------------------------------------
-// rolled variant for the large classes (L = la+lb+lc+ld >= ROLL_L)
+// rolled variant for the largest classes (L = la+lb+lc+ld >= ROLL_L)
 // ---------------------------------------------------------------------------
 //
 // The same arithmetic as k_eri, with the Cartesian and Hermite loops kept as
@@ -510,7 +510,7 @@ k_eri(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra, con
 // operations per thread, far past the register file; on GB300 the FP64
 // kernels are bound by the FP64 pipe, so the loop overhead is hidden there.
 
-constexpr int ROLL_L = 6;
+constexpr int ROLL_L = 7;
 
 template <int L, typename R>
 __device__ __forceinline__ void hermite_r_rolled(R* Rt, const R* G, R X, R Y, R Z) {

@@ -50,17 +50,75 @@ __device__ __forceinline__ bool above(float x, float lthr, double thr, const dou
     return __dmul_rn(__dmul_rn(snorm[ab], pnorm[bd]), snorm[cd]) > thr;
 }
 
+constexpr int EXP_WARPS = 8;     // warps per block
+constexpr int STAGE = 16;        // shells per leaf held in the shared tables
+
+// q = x / n for x < 2^16 and 2 <= n <= 16 by q = mulhi(x, m), m = floor(2^32/n) + 1
+// (exact in that range); n = 1 is passed as m = 0 and returns x.
+struct Div {
+    unsigned m;
+    __device__ explicit Div(int n) : m(n > 1 ? 0xffffffffu / (unsigned)n + 1u : 0u) {}
+};
+__device__ __forceinline__ unsigned fdiv(unsigned x, Div d) { return d.m ? __umulhi(x, d.m) : x; }
+
+struct WarpTables {
+    float sab[STAGE * STAGE];    // log2 S_ab, [ia][ib]
+    float scd[STAGE * STAGE];    // log2 S_cd, [ic][id]
+    float pbd[STAGE * STAGE];    // log2 ||P_bd||, [ib][id]
+    uint8_t cab[STAGE * STAGE];  // pair class la*3+lb
+    uint8_t ccd[STAGE * STAGE];
+};
+
+// Decides one candidate and returns its stream (-1 = culled).
+__device__ __forceinline__ int decide(const ExpandArgs& p, float x, int a, int b, int c, int d, int cls,
+                                      int32_t& pab, int32_t& pcd) {
+    const int64_t ab = (int64_t)a * p.ns + b, bd = (int64_t)b * p.ns + d, cd = (int64_t)c * p.ns + d;
+    bool keep = p.screen ? above(x, p.ltau, p.tau, p.snorm, p.pnorm, ab, bd, cd) : true;
+    if (!keep) return -1;
+    pab = __ldg(p.pairmap + ab);
+    pcd = __ldg(p.pairmap + cd);
+    if (pab < 0 || pcd < 0) return -1;
+    int prec = 0;
+    if (p.mixed) prec = above(x, p.lsplit, p.split, p.snorm, p.pnorm, ab, bd, cd) ? 0 : 1;
+    return prec * NCLASS + cls;
+}
+
 template <bool WRITE>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void emit(int stream, int32_t pab, int32_t pcd, int lane, unsigned int* scount,
+                                     unsigned long long* __restrict__ ctr, Quartet* __restrict__ rec,
+                                     const unsigned long long* __restrict__ end,
+                                     unsigned long long* __restrict__ err) {
+    if (WRITE) {
+        const unsigned keepmask = __ballot_sync(0xffffffffu, stream >= 0);
+        if (stream >= 0) {
+            const unsigned grp = __match_any_sync(keepmask, stream);
+            const int leader = __ffs(grp) - 1;
+            unsigned long long bas = 0;
+            if (lane == leader) bas = atomicAdd(ctr + stream, (unsigned long long)__popc(grp));
+            bas = __shfl_sync(grp, bas, leader);
+            const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+            // the count pass sized every stream; never write past it
+            if (bas + rank < end[stream]) rec[bas + rank] = Quartet{pab, pcd};
+            else atomicAdd(err, 1ull);
+        }
+    } else {
+        if (stream >= 0) atomicAdd(&scount[stream], 1u);
+    }
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(EXP_WARPS * 32)
 k_expand(ExpandArgs p, unsigned long long* __restrict__ ctr, Quartet* __restrict__ rec,
          unsigned long long* __restrict__ cand, const unsigned long long* __restrict__ end,
          unsigned long long* __restrict__ err) {
     __shared__ unsigned int scount[2 * NCLASS];
+    __shared__ WarpTables tabs[EXP_WARPS];
     if (!WRITE) {
         for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x) scount[i] = 0;
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
+    WarpTables& tb = tabs[threadIdx.x >> 5];
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long ncand = 0;
@@ -72,48 +130,68 @@ k_expand(ExpandArgs p, unsigned long long* __restrict__ ctr, Quartet* __restrict
         const int d0 = p.llo[t.d], nd = p.lhi[t.d] - d0;
         const int total = na * nb * nc * nd;
         ncand += total;
-        for (int base = 0; base < total; base += 32) {
-            const int idx = base + lane;
-            int stream = -1;
-            int32_t pab = -1, pcd = -1;
-            if (idx < total) {
-                int r = idx;
-                const int id = r % nd; r /= nd;
-                const int ib = r % nb; r /= nb;
-                const int ic = r % nc;
-                const int ia = r / nc;
-                const int a = a0 + ia, b = b0 + ib, c = c0 + ic, d = d0 + id;
-                const int64_t ab = (int64_t)a * p.ns + b, bd = (int64_t)b * p.ns + d, cd = (int64_t)c * p.ns + d;
-                float x = 0.f;
-                if (p.screen || p.mixed) x = p.slog[ab] + p.plog[bd] + p.slog[cd];
-                bool keep = p.screen ? above(x, p.ltau, p.tau, p.snorm, p.pnorm, ab, bd, cd) : true;
-                if (keep) {
-                    pab = p.pairmap[ab];
-                    pcd = p.pairmap[cd];
-                    keep = pab >= 0 && pcd >= 0;
-                }
-                if (keep) {
-                    const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
-                    int prec = 0;
-                    if (p.mixed) prec = above(x, p.lsplit, p.split, p.snorm, p.pnorm, ab, bd, cd) ? 0 : 1;
-                    stream = prec * NCLASS + cls;
-                }
+        const Div md(nd), mb(nb), mc(nc);
+        if (na <= STAGE && nb <= STAGE && nc <= STAGE && nd <= STAGE && total < 65536) {
+            // stage the leaf quartet's log tables and pair classes
+            __syncwarp();
+            for (int k = lane; k < na * nb; k += 32) {
+                const int ia = fdiv(k, mb), ib = k - ia * nb;
+                const int a = a0 + ia, b = b0 + ib;
+                tb.sab[ia * STAGE + ib] = __ldg(p.slog + (int64_t)a * p.ns + b);
+                tb.cab[ia * STAGE + ib] = (uint8_t)(__ldg(p.tl + a) * 3 + __ldg(p.tl + b));
             }
-            if (WRITE) {
-                const unsigned keepmask = __ballot_sync(0xffffffffu, stream >= 0);
-                if (stream >= 0) {
-                    const unsigned grp = __match_any_sync(keepmask, stream);
-                    const int leader = __ffs(grp) - 1;
-                    unsigned long long bas = 0;
-                    if (lane == leader) bas = atomicAdd(ctr + stream, (unsigned long long)__popc(grp));
-                    bas = __shfl_sync(grp, bas, leader);
-                    const unsigned rank = __popc(grp & ((1u << lane) - 1u));
-                    // the count pass sized every stream; never write past it
-                    if (bas + rank < end[stream]) rec[bas + rank] = Quartet{pab, pcd};
-                    else atomicAdd(err, 1ull);
+            for (int k = lane; k < nc * nd; k += 32) {
+                const int ic = fdiv(k, md), id = k - ic * nd;
+                const int c = c0 + ic, d = d0 + id;
+                tb.scd[ic * STAGE + id] = __ldg(p.slog + (int64_t)c * p.ns + d);
+                tb.ccd[ic * STAGE + id] = (uint8_t)(__ldg(p.tl + c) * 3 + __ldg(p.tl + d));
+            }
+            for (int k = lane; k < nb * nd; k += 32) {
+                const int ib = fdiv(k, md), id = k - ib * nd;
+                tb.pbd[ib * STAGE + id] = __ldg(p.plog + (int64_t)(b0 + ib) * p.ns + d0 + id);
+            }
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                const unsigned idx = base + lane;
+                int stream = -1;
+                int32_t pab = -1, pcd = -1;
+                if (idx < (unsigned)total) {
+                    // (ia, ic, ib, id), id fastest
+                    const unsigned r1 = fdiv(idx, md);
+                    const int id = idx - r1 * nd;
+                    const unsigned r2 = fdiv(r1, mb);
+                    const int ib = r1 - r2 * nb;
+                    const unsigned ia = fdiv(r2, mc);
+                    const int ic = r2 - ia * nc;
+                    float x = 0.f;
+                    if (p.screen || p.mixed)
+                        x = tb.sab[ia * STAGE + ib] + tb.pbd[ib * STAGE + id] + tb.scd[ic * STAGE + id];
+                    const int cls = tb.cab[ia * STAGE + ib] * 9 + tb.ccd[ic * STAGE + id];
+                    stream = decide(p, x, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, pab, pcd);
                 }
-            } else {
-                if (stream >= 0) atomicAdd(&scount[stream], 1u);
+                emit<WRITE>(stream, pab, pcd, lane, scount, ctr, rec, end, err);
+            }
+        } else {
+            // very large leaves: read the tables from global memory
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + lane;
+                int stream = -1;
+                int32_t pab = -1, pcd = -1;
+                if (idx < total) {
+                    int r = idx;
+                    const int id = r % nd; r /= nd;
+                    const int ib = r % nb; r /= nb;
+                    const int ic = r % nc;
+                    const int ia = r / nc;
+                    const int a = a0 + ia, b = b0 + ib, c = c0 + ic, d = d0 + id;
+                    float x = 0.f;
+                    if (p.screen || p.mixed)
+                        x = p.slog[(int64_t)a * p.ns + b] + p.plog[(int64_t)b * p.ns + d] +
+                            p.slog[(int64_t)c * p.ns + d];
+                    const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
+                    stream = decide(p, x, a, b, c, d, cls, pab, pcd);
+                }
+                emit<WRITE>(stream, pab, pcd, lane, scount, ctr, rec, end, err);
             }
         }
     }
@@ -150,8 +228,7 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
 }
 
 static unsigned expand_grid(int64_t n) {
-    int64_t warps = n;
-    int64_t blocks = (warps + 7) / 8;
+    int64_t blocks = (n + EXP_WARPS - 1) / EXP_WARPS;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
 }
 
@@ -159,7 +236,7 @@ int expand_count(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
                  unsigned long long* d_count) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<false><<<expand_grid(n), 256, 0, c->stream>>>(a, d_count, nullptr, c->d_counters + CTR_CAND, nullptr,
+    k_expand<false><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, d_count, nullptr, c->d_counters + CTR_CAND, nullptr,
                                                             nullptr);
     return KX_OK;
 }
@@ -168,7 +245,7 @@ int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
                  unsigned long long* d_cursor, Quartet* rec) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<true><<<expand_grid(n), 256, 0, c->stream>>>(a, d_cursor, rec, nullptr, c->d_counters + CTR_END,
+    k_expand<true><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, d_cursor, rec, nullptr, c->d_counters + CTR_END,
                                                            c->d_counters + CTR_ERR);
     return KX_OK;
 }
