@@ -33,7 +33,7 @@ METRIC = "K-builds/s & ERI quartets/s vs plain FP64 GPU path at max|ΔK|≤1e-8"
 UNIT = "K-builds/s"
 WORKLOAD = "water64"
 TAU = 1e-10
-SPLIT = 1e-5
+SPLIT = 1e-4
 L2_FLUSH_BYTES = 256 << 20
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
