@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "K-builds/s & ERI quartets/s vs plain FP64 GPU path at max|ΔK|≤1e-8"
 UNIT = "K-builds/s"
-WORKLOAD = "water64"
+WORKLOADS = ("water64", "water16")
 TAU = 1e-10
 SPLIT = 1e-4
 L2_FLUSH_BYTES = 256 << 20
@@ -137,7 +137,7 @@ def run_reference(args):
     if rank != 0:
         return
     import workloads as wl
-    sys_, P = wl.workload(WORKLOAD)
+    sys_, P = wl.workload(args.workload)
     # warm-up steps and timed steps, each a bounded sample of the workload
     times = []
     rates = []
@@ -152,15 +152,17 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(sys_, "fp64"),
+            "data": "synthetic", "config": workload_config(sys_, "fp64", args.workload),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def workload_config(sys_, precision):
-    return {"workload": f"(H2O)64 water cluster at 1 g/cm^3, even-tempered medium basis "
+def workload_config(sys_, precision, name):
+    nw = sys_.n_atom // 3
+    return {"workload": f"(H2O){nw} water cluster at 1 g/cm^3, even-tempered medium basis "
                         f"({sys_.n_fn} functions, {sys_.n_shell} shells), tau=1e-10",
+            "name": name,
             "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": 10,
             "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
             "shell_screen": True,
@@ -186,7 +188,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     kx.load()
-    sys_, P = wl.workload(WORKLOAD)
+    sys_, P = wl.workload(args.workload)
     stream = torch.cuda.current_stream(dev)
     ex = kx.Exchange(sys_, device=local, stream=stream)
     n = sys_.n_fn
@@ -305,7 +307,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": workload_config(sys_, "mixed"),
+            "config": workload_config(sys_, "mixed", args.workload),
             "quartets_per_s": ws * quartets / (ms_step * 1e-3),
             "shell_quartets": quartets, "leaf_quartets": st.n_leaf_quartets,
             "shell_quartets_fp64": st.n_shell_quartets_fp64,
@@ -343,6 +345,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=WORKLOADS, default="water64",
+                    help="water64 is the benchmark; water16 is a small case for profiling")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-rows", type=int, default=2, help="K-row shells per oracle sample")

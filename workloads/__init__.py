@@ -357,6 +357,8 @@ def random_shells(n: int, seed: int, lmax: int = 2, box: float = 3.0,
 WORKLOADS = {
     "water4": dict(make=lambda: water4(1), p_seed=1001, taus=(0.0, 1e-10)),
     "water64": dict(make=lambda: water64(2), p_seed=1002, taus=(1e-10,)),
+    # a smaller cluster with the same basis and density generator
+    "water16": dict(make=lambda: water_cluster(16, 16, "medium"), p_seed=1016, taus=(1e-10,)),
 }
 
 
