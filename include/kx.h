@@ -172,6 +172,46 @@ int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32
  * Not part of the exchange build; used to state roofline fractions. */
 int kx_peak_probe(int device, int precision, double* gflops);
 
+/* Largest frontier, in tasks, that kx_traverse_level_noalloc accepts. */
+#define KX_NOALLOC_MAX_TASKS (1 << 18)
+
+/* One level of the hextree traversal that allocates no device memory.
+ *
+ * This entry point has no counterpart in the paper.  It exists for callers
+ * that cannot let a library allocate: programs that hand all device memory
+ * to their own allocator at start-up (a framework's caching pool, or a fixed
+ * budget reserved once) and must not see cudaMalloc/cudaFree calls behind
+ * their back, and programs with a no-allocation-after-initialisation rule
+ * (a cudaMalloc or cudaFree can stall the whole device).
+ *
+ * It expands the n level-`level` tasks of `front` (DEVICE array of n tasks,
+ * each four uint16 node ids A, B, C, D of that level, as in the traversal of
+ * kx_exchange) into the level-(level+1) tasks whose Eq. 8 bound exceeds tau,
+ * written to `next` (DEVICE array with room for cap tasks) in the order the
+ * traversal uses; *n_next (host) receives their number.  Starting from the
+ * single task (0,0,0,0) at level 0 and calling it for levels 0 .. depth-1
+ * yields the leaf-quartet worklist of kx_exchange for the same tau.
+ *
+ * Requirements: a tree (kx_build_tree) and the P norms of a previous
+ * kx_exchange on this context (the norms of that call's P are used).
+ * Scratch: a file-scope device array of 4.5 MiB, holding counts,
+ * offsets, masks and scan sums for up to KX_NOALLOC_MAX_TASKS tasks, that
+ * every GPU which loads the library keeps until the process exits.  The
+ * first call on a device (made current by the call) looks up that array's
+ * device address; make that first call before any stream capture on the
+ * device.  All calls share the array and it keeps the last call's contents
+ * (the call itself clears what must start at zero), so calls that overlap
+ * on the GPU -- other streams, threads or contexts on the same device --
+ * race and must be serialised by the caller.  Returns after the count is on
+ * the host.
+ *
+ * Errors: KX_ECAPACITY when n > KX_NOALLOC_MAX_TASKS (nothing is run) or
+ * when the next frontier exceeds cap (the first cap tasks are written and
+ * *n_next holds the full count); KX_ESTATE without tree or P norms;
+ * KX_EINVAL for a bad level, pointer, size or tau. */
+int kx_traverse_level_noalloc(kx_ctx* c, int32_t level, const uint16_t* front, int64_t n,
+                              double tau, uint16_t* next, int64_t cap, int64_t* n_next);
+
 /* Last error message of the context (never NULL). */
 const char* kx_last_error(const kx_ctx* c);
 

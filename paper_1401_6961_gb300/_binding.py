@@ -22,7 +22,9 @@ ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "K
 # every entry point declared in include/kx.h
 EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
            "kx_exchange_host", "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
-           "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_last_error", "kx_destroy"]
+           "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
+           "kx_last_error", "kx_destroy"]
+KX_NOALLOC_MAX_TASKS = 1 << 18
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -97,6 +99,8 @@ def load() -> ctypes.CDLL:
     L.kx_get_norms.argtypes = [vp, _f64p, _f64p]
     L.kx_get_profile.argtypes = [vp, _f64p, _i64p, _f64p, _i32p]
     L.kx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _f64p]
+    L.kx_traverse_level_noalloc.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_double, vp,
+                                            ctypes.c_int64, _i64p]
     L.kx_last_error.argtypes = [vp]
     L.kx_last_error.restype = ctypes.c_char_p
     L.kx_destroy.argtypes = [vp]
@@ -240,6 +244,16 @@ def kx_peak_probe(device: int = 0, precision: int = KX_FP64) -> float:
     if r != KX_OK:
         raise KxError(r, "kx_peak_probe failed")
     return float(g.value)
+
+
+def kx_traverse_level_noalloc(ctx, level: int, front_ptr: int, n: int, tau: float, next_ptr: int,
+                              cap: int) -> int:
+    """One traversal level without allocation; device pointers to uint16
+    task arrays ([n][4] in, [cap][4] out).  Returns the next frontier size."""
+    nn = ctypes.c_int64()
+    _check(ctx, load().kx_traverse_level_noalloc(ctx, int(level), ctypes.c_void_p(front_ptr), int(n), float(tau),
+                                                 ctypes.c_void_p(next_ptr), int(cap), ctypes.byref(nn)))
+    return int(nn.value)
 
 
 def kx_last_error(ctx) -> str:
