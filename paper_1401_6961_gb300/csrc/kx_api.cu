@@ -46,7 +46,7 @@ void free_all(kx_ctx* c) {
                     c->d_pq, c->d_pnorm, c->d_plog, c->d_node_lo, c->d_node_hi, c->d_node_child,
                     c->d_node_nchild, c->d_sq_s, c->d_sq_p, c->d_nrm_s, c->d_nrm_p, c->d_leaf_lo, c->d_leaf_hi,
                     c->d_boys64, c->d_boys32, c->d_pairmap, c->d_scratch, c->d_front[0], c->d_front[1],
-                    c->d_mask, c->d_scan, c->d_rec, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
+                    c->d_mask, c->d_scan, c->d_rec, c->d_bin, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
                     c->d_hostP, c->d_hostK};
     for (void* p : ptrs)
         if (p) cudaFree(p);

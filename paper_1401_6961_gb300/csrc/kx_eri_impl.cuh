@@ -105,20 +105,36 @@ __device__ __forceinline__ void boys_scaled(R* G, R T, R rho, R r2, R pref, cons
     if (T < R(BOYS_TMAX)) {
         int ig = Real<R>::rnd(T * R(BOYS_DENS));
         R d = T - R(ig) * R(1.0 / BOYS_DENS);
-        const R* row = tab + ig * (BOYS_M + 1);
         R md[6];
         sfor<6>([&](auto k_) {
             constexpr int k = KX_CV(k_);
             md[k] = -d * R(1.0 / (k + 1));
         });
+        // the L+7 table values F_0..F_{L+6}(T_i) of the row
+        R rv[L + 7];
+        if constexpr (sizeof(R) == 4) {
+            constexpr int NV = (L + 7 + 3) / 4;
+            const float4* row4 = reinterpret_cast<const float4*>(tab + ig * BOYS32_ROW);
+            sfor<NV>([&](auto v_) {
+                constexpr int v = KX_CV(v_);
+                const float4 q = __ldg(row4 + v);
+                if constexpr (4 * v + 0 < L + 7) rv[4 * v + 0] = q.x;
+                if constexpr (4 * v + 1 < L + 7) rv[4 * v + 1] = q.y;
+                if constexpr (4 * v + 2 < L + 7) rv[4 * v + 2] = q.z;
+                if constexpr (4 * v + 3 < L + 7) rv[4 * v + 3] = q.w;
+            });
+        } else {
+            const R* row = tab + ig * (BOYS_M + 1);
+            sfor<L + 7>([&](auto k_) { rv[KX_CV(k_)] = __ldg(row + KX_CV(k_)); });
+        }
         R s = pref;
         const R m2r = R(-2) * rho;
         sfor<L + 1>([&](auto m_) {
             constexpr int m = KX_CV(m_);
-            R acc = __ldg(row + m + 6);
+            R acc = rv[m + 6];
             sfor<6>([&](auto k_) {
                 constexpr int k = 5 - KX_CV(k_);
-                acc = __ldg(row + m + k) + acc * md[k];
+                acc = rv[m + k] + acc * md[k];
             });
             G[m] = s * acc;
             if constexpr (m < L) s *= m2r;
@@ -183,6 +199,92 @@ __device__ __forceinline__ void hermite_r(R* Rt, const R* G, R X, R Y, R Z) {
         });
         Rt[0] = G[n];
     });
+}
+
+// ---------------------------------------------------------------------------
+// pair data
+// ---------------------------------------------------------------------------
+
+// record stride of a pair class in the FP64 and FP32 tables
+template <typename R>
+__host__ __device__ constexpr int rec_stride(int la, int lb) {
+    return sizeof(R) == 8 ? pair_stride(la, lb) : PAIR32_STRIDE;
+}
+
+// E^{ij}_t of one dimension (layout eidx(LA,LB,i,j,t)) by the recursions
+//   E^{i+1,j}_t = E^{ij}_{t-1}/(2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
+//   E^{i,j+1}_t = E^{ij}_{t-1}/(2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1},
+// unrolled; entries outside t <= i+j are zero.
+template <int LA, int LB>
+__device__ __forceinline__ void e_build(float* E, float xpa, float xpb, float inv2p) {
+    sfor<etab(LA, LB)>([&](auto k_) { E[KX_CV(k_)] = 0.f; });
+    E[eidx(LA, LB, 0, 0, 0)] = 1.f;
+    sfor<LA + 1>([&](auto i_) {
+        constexpr int i = KX_CV(i_);
+        if constexpr (i > 0) {
+            sfor<i + 1>([&](auto t_) {
+                constexpr int t = KX_CV(t_);
+                float v = 0.f;
+                if constexpr (t <= i - 1) v = xpa * E[eidx(LA, LB, i - 1, 0, t)];
+                if constexpr (t > 0) v += inv2p * E[eidx(LA, LB, i - 1, 0, t - 1)];
+                if constexpr (t + 1 <= i - 1) v += float(t + 1) * E[eidx(LA, LB, i - 1, 0, t + 1)];
+                E[eidx(LA, LB, i, 0, t)] = v;
+            });
+        }
+        sfor<LB>([&](auto jj_) {
+            constexpr int j = KX_CV(jj_) + 1;
+            sfor<i + j + 1>([&](auto t_) {
+                constexpr int t = KX_CV(t_);
+                float v = 0.f;
+                if constexpr (t <= i + j - 1) v = xpb * E[eidx(LA, LB, i, j - 1, t)];
+                if constexpr (t > 0) v += inv2p * E[eidx(LA, LB, i, j - 1, t - 1)];
+                if constexpr (t + 1 <= i + j - 1) v += float(t + 1) * E[eidx(LA, LB, i, j - 1, t + 1)];
+                E[eidx(LA, LB, i, j, t)] = v;
+            });
+        });
+    });
+}
+
+// Loads the bra and ket pairs of a quartet: exponent sums, prefactors,
+// P - Q and the per-dimension E tables (E[x*etab + ...]).
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void load_pairs(const R* __restrict__ pb, const R* __restrict__ pk, R* eab, R* ecd, R& p,
+                                           R& qq, R& kab, R& kcd, R& X, R& Y, R& Z) {
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    if constexpr (sizeof(R) == 8) {
+        sfor<3 * EAB>([&](auto k_) { eab[KX_CV(k_)] = __ldg(pb + 5 + KX_CV(k_)); });
+        sfor<3 * ECD>([&](auto k_) { ecd[KX_CV(k_)] = __ldg(pk + 5 + KX_CV(k_)); });
+        p = __ldg(pb);
+        qq = __ldg(pk);
+        X = __ldg(pb + 1) - __ldg(pk + 1);
+        Y = __ldg(pb + 2) - __ldg(pk + 2);
+        Z = __ldg(pb + 3) - __ldg(pk + 3);
+        kab = __ldg(pb + 4);
+        kcd = __ldg(pk + 4);
+    } else {
+        const float4* b4 = reinterpret_cast<const float4*>(pb);
+        const float4* k4 = reinterpret_cast<const float4*>(pk);
+        float b[16], k[16];
+        sfor<4>([&](auto v_) {
+            constexpr int v = KX_CV(v_);
+            const float4 x = __ldg(b4 + v), y = __ldg(k4 + v);
+            b[4 * v] = x.x; b[4 * v + 1] = x.y; b[4 * v + 2] = x.z; b[4 * v + 3] = x.w;
+            k[4 * v] = y.x; k[4 * v + 1] = y.y; k[4 * v + 2] = y.z; k[4 * v + 3] = y.w;
+        });
+        p = b[P32_P];
+        qq = k[P32_P];
+        kab = b[P32_KAB];
+        kcd = k[P32_KAB];
+        // (hi_P - hi_Q) is exact when P ~ Q; the lo parts restore the rest
+        X = (b[P32_PHI] - k[P32_PHI]) + (b[P32_PLO] - k[P32_PLO]);
+        Y = (b[P32_PHI + 1] - k[P32_PHI + 1]) + (b[P32_PLO + 1] - k[P32_PLO + 1]);
+        Z = (b[P32_PHI + 2] - k[P32_PHI + 2]) + (b[P32_PLO + 2] - k[P32_PLO + 2]);
+        sfor<3>([&](auto x_) {
+            constexpr int x = KX_CV(x_);
+            e_build<LA, LB>(eab + x * EAB, b[P32_PA + x], b[P32_PB + x], b[P32_INV2P]);
+            e_build<LC, LD>(ecd + x * ECD, k[P32_PA + x], k[P32_PB + x], k[P32_INV2P]);
+        });
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -462,7 +564,7 @@ k_eri(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra, con
       const R* __restrict__ P, int64_t ldp, double* __restrict__ K, int64_t ldk, int64_t nab, int64_t ncd) {
     constexpr int NA = ncart(LA), NC = ncart(LC);
     constexpr int L = LA + LB + LC + LD;
-    constexpr int SAB = pair_stride(LA, LB), SCD = pair_stride(LC, LD);
+    constexpr int SAB = rec_stride<R>(LA, LB), SCD = rec_stride<R>(LC, LD);
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
     const int64_t i = blockIdx.x * (int64_t)ERI_THREADS + threadIdx.x;
     R kacc[NA * NC];
@@ -477,17 +579,13 @@ k_eri(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra, con
         fa = mb.fa;
         fc = mk.fa;
         R eab[3 * EAB], ecd[3 * ECD];
-        sfor<3 * EAB>([&](auto k_) { eab[KX_CV(k_)] = __ldg(pb + 5 + KX_CV(k_)); });
-        sfor<3 * ECD>([&](auto k_) { ecd[KX_CV(k_)] = __ldg(pk + 5 + KX_CV(k_)); });
-        const R p = __ldg(pb), qq = __ldg(pk);
-        const R X = __ldg(pb + 1) - __ldg(pk + 1);
-        const R Y = __ldg(pb + 2) - __ldg(pk + 2);
-        const R Z = __ldg(pb + 3) - __ldg(pk + 3);
+        R p, qq, kab, kcd, X, Y, Z;
+        load_pairs<LA, LB, LC, LD, R>(pb, pk, eab, ecd, p, qq, kab, kcd, X, Y, Z);
         const R pq = p * qq, sum = p + qq;
         const R rho = pq / sum;
         const R r2 = X * X + Y * Y + Z * Z;
         const R T = rho * r2;
-        const R pref = R(2.0 * 17.493418327624862) * __ldg(pb + 4) * __ldg(pk + 4) / (pq * Real<R>::sqrt_(sum));
+        const R pref = R(2.0 * 17.493418327624862) * kab * kcd / (pq * Real<R>::sqrt_(sum));
         R G[L + 1];
         boys_scaled<L, R>(G, T, rho, r2, pref, boys);
         R Rt[nherm(L)];
@@ -692,7 +790,7 @@ k_eri_rolled(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ b
              int64_t ldk, int64_t nab, int64_t ncd) {
     constexpr int NA = ncart(LA), NC = ncart(LC);
     constexpr int L = LA + LB + LC + LD;
-    constexpr int SAB = pair_stride(LA, LB), SCD = pair_stride(LC, LD);
+    constexpr int SAB = rec_stride<R>(LA, LB), SCD = rec_stride<R>(LC, LD);
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
     const int64_t i = blockIdx.x * (int64_t)ERI_THREADS + threadIdx.x;
     R kacc[NA * NC];
@@ -708,19 +806,13 @@ k_eri_rolled(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ b
         fa = mb.fa;
         fc = mk.fa;
         R eab[3 * EAB], ecd[3 * ECD];
-#pragma unroll 1
-        for (int k = 0; k < 3 * EAB; ++k) eab[k] = __ldg(pb + 5 + k);
-#pragma unroll 1
-        for (int k = 0; k < 3 * ECD; ++k) ecd[k] = __ldg(pk + 5 + k);
-        const R p = __ldg(pb), qq = __ldg(pk);
-        const R X = __ldg(pb + 1) - __ldg(pk + 1);
-        const R Y = __ldg(pb + 2) - __ldg(pk + 2);
-        const R Z = __ldg(pb + 3) - __ldg(pk + 3);
+        R p, qq, kab, kcd, X, Y, Z;
+        load_pairs<LA, LB, LC, LD, R>(pb, pk, eab, ecd, p, qq, kab, kcd, X, Y, Z);
         const R pq = p * qq, sum = p + qq;
         const R rho = pq / sum;
         const R r2 = X * X + Y * Y + Z * Z;
         const R T = rho * r2;
-        const R pref = R(2.0 * 17.493418327624862) * __ldg(pb + 4) * __ldg(pk + 4) / (pq * Real<R>::sqrt_(sum));
+        const R pref = R(2.0 * 17.493418327624862) * kab * kcd / (pq * Real<R>::sqrt_(sum));
         R G[L + 1];
         boys_scaled<L, R>(G, T, rho, r2, pref, boys);
         R Rt[nherm(L)];

@@ -15,8 +15,10 @@
 // Records are binned by angular-momentum class and precision ("stream",
 // 162 of them).  One warp handles one leaf quartet; lanes walk its shell
 // quartets with d fastest, then b, c, a, so runs of equal (a,c) -- one K
-// block -- stay adjacent in each stream.  A first pass counts per stream, a
-// second writes through per-stream cursors with warp-aggregated atomics.
+// block -- stay adjacent in each stream.  A first pass counts the records of
+// every (stream, block); after a scan of those counts a second pass writes
+// each block's records from its offsets through shared-memory cursors, so no
+// global atomic is involved and the blocks' ranges are fixed.
 #include <algorithm>
 #include <cmath>
 
@@ -53,8 +55,9 @@ __device__ __forceinline__ bool above(float x, float lthr, double thr, const dou
 constexpr int EXP_WARPS = 8;     // warps per block
 constexpr int STAGE = 16;        // shells per leaf held in the shared tables
 
-// q = x / n for x < 2^16 and 2 <= n <= 16 by q = mulhi(x, m), m = floor(2^32/n) + 1
-// (exact in that range); n = 1 is passed as m = 0 and returns x.
+// q = x / n for x < 2^16 and 2 <= n < 2^16 by q = mulhi(x, m), m = floor(2^32/n) + 1:
+// x*m/2^32 = x/n + x*e/2^32 with 0 < e < 1, and x/2^32 < 1/n keeps the floor
+// exact; n = 1 is passed as m = 0 and returns x.
 struct Div {
     unsigned m;
     __device__ explicit Div(int n) : m(n > 1 ? 0xffffffffu / (unsigned)n + 1u : 0u) {}
@@ -65,58 +68,71 @@ struct WarpTables {
     float sab[STAGE * STAGE];    // log2 S_ab, [ia][ib]
     float scd[STAGE * STAGE];    // log2 S_cd, [ic][id]
     float pbd[STAGE * STAGE];    // log2 ||P_bd||, [ib][id]
+    float mb[STAGE];             // max over a of log2 S_ab, per b
+    float md[STAGE];             // max over c of log2 S_cd, per d
     uint8_t cab[STAGE * STAGE];  // pair class la*3+lb
     uint8_t ccd[STAGE * STAGE];
+    uint8_t kl[STAGE * STAGE];   // (b,d) pairs that can pass for some (a,c): ib*16+id
 };
 
-// Decides one candidate and returns its stream (-1 = culled).
-__device__ __forceinline__ int decide(const ExpandArgs& p, float x, int a, int b, int c, int d, int cls,
-                                      int32_t& pab, int32_t& pcd) {
+// Decides one candidate and returns its stream (-1 = culled).  The pair
+// tables hold every pair of a kept quartet (their filter is looser than the
+// quartet test), so only the write pass reads the slots.  Without the shell
+// screen a quartet is kept unless one of its pairs is empty (Eq. 4), which
+// the -inf logs of zero Schwarz factors tell.
+template <bool WRITE>
+__device__ __forceinline__ int decide(const ExpandArgs& p, float x, float sab, float scd, int a, int b, int c,
+                                      int d, int cls, int32_t& pab, int32_t& pcd) {
     const int64_t ab = (int64_t)a * p.ns + b, bd = (int64_t)b * p.ns + d, cd = (int64_t)c * p.ns + d;
-    bool keep = p.screen ? above(x, p.ltau, p.tau, p.snorm, p.pnorm, ab, bd, cd) : true;
+    const bool keep = p.screen ? above(x, p.ltau, p.tau, p.snorm, p.pnorm, ab, bd, cd)
+                               : (sab > -INFINITY && scd > -INFINITY);
     if (!keep) return -1;
-    pab = __ldg(p.pairmap + ab);
-    pcd = __ldg(p.pairmap + cd);
-    if (pab < 0 || pcd < 0) return -1;
+    if (WRITE) {
+        pab = __ldg(p.pairmap + ab);
+        pcd = __ldg(p.pairmap + cd);
+    }
     int prec = 0;
     if (p.mixed) prec = above(x, p.lsplit, p.split, p.snorm, p.pnorm, ab, bd, cd) ? 0 : 1;
     return prec * NCLASS + cls;
 }
 
+// One warp-aggregated shared-memory add per distinct stream of the lanes
+// kept candidates.  Count pass: per-block totals.  Write pass: the block's
+// cursor of that stream gives the slot of every lane's record.
 template <bool WRITE>
 __device__ __forceinline__ void emit(int stream, int32_t pab, int32_t pcd, int lane, unsigned int* scount,
-                                     unsigned long long* __restrict__ ctr, Quartet* __restrict__ rec,
-                                     const unsigned long long* __restrict__ end,
+                                     Quartet* __restrict__ rec, const unsigned long long* __restrict__ end,
                                      unsigned long long* __restrict__ err) {
-    if (WRITE) {
-        const unsigned keepmask = __ballot_sync(0xffffffffu, stream >= 0);
-        if (stream >= 0) {
-            const unsigned grp = __match_any_sync(keepmask, stream);
-            const int leader = __ffs(grp) - 1;
-            unsigned long long bas = 0;
-            if (lane == leader) bas = atomicAdd(ctr + stream, (unsigned long long)__popc(grp));
-            bas = __shfl_sync(grp, bas, leader);
-            const unsigned rank = __popc(grp & ((1u << lane) - 1u));
-            // the count pass sized every stream; never write past it
-            if (bas + rank < end[stream]) rec[bas + rank] = Quartet{pab, pcd};
-            else atomicAdd(err, 1ull);
-        }
-    } else {
+    if (!WRITE) {
         if (stream >= 0) atomicAdd(&scount[stream], 1u);
+        return;
+    }
+    const unsigned keepmask = __ballot_sync(0xffffffffu, stream >= 0);
+    if (stream < 0) return;
+    const unsigned grp = __match_any_sync(keepmask, stream);
+    const int leader = __ffs(grp) - 1;
+    unsigned bas = 0;
+    if (lane == leader) bas = atomicAdd(&scount[stream], (unsigned)__popc(grp));
+    if (WRITE) {
+        bas = __shfl_sync(grp, bas, leader);
+        const unsigned long long slot = (unsigned long long)bas + __popc(grp & ((1u << lane) - 1u));
+        // the count pass sized every (stream, block) range; never write past the stream
+        if (slot < end[stream]) rec[slot] = Quartet{pab, pcd};
+        else atomicAdd(err, 1ull);
     }
 }
 
 template <bool WRITE>
 __global__ void __launch_bounds__(EXP_WARPS * 32)
-k_expand(ExpandArgs p, unsigned long long* __restrict__ ctr, Quartet* __restrict__ rec,
-         unsigned long long* __restrict__ cand, const unsigned long long* __restrict__ end,
-         unsigned long long* __restrict__ err) {
+k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, unsigned long long* __restrict__ cand,
+         const unsigned long long* __restrict__ end, unsigned long long* __restrict__ err) {
+    // bin[s * gridDim.x + block]: count pass writes the block's count of
+    // stream s, the write pass reads the scanned offset
     __shared__ unsigned int scount[2 * NCLASS];
     __shared__ WarpTables tabs[EXP_WARPS];
-    if (!WRITE) {
-        for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x) scount[i] = 0;
-        __syncthreads();
-    }
+    for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x)
+        scount[i] = WRITE ? (unsigned)bin[(int64_t)i * gridDim.x + blockIdx.x] : 0u;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     WarpTables& tb = tabs[threadIdx.x >> 5];
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -151,25 +167,60 @@ k_expand(ExpandArgs p, unsigned long long* __restrict__ ctr, Quartet* __restrict
                 tb.pbd[ib * STAGE + id] = __ldg(p.plog + (int64_t)(b0 + ib) * p.ns + d0 + id);
             }
             __syncwarp();
-            for (int base = 0; base < total; base += 32) {
+            // column maxima for the (b,d) pre-filter
+            if (lane < nb) {
+                float m = -INFINITY;
+                for (int ia = 0; ia < na; ++ia) m = fmaxf(m, tb.sab[ia * STAGE + lane]);
+                tb.mb[lane] = m;
+            }
+            if (lane < nd) {
+                float m = -INFINITY;
+                for (int ic = 0; ic < nc; ++ic) m = fmaxf(m, tb.scd[ic * STAGE + lane]);
+                tb.md[lane] = m;
+            }
+            __syncwarp();
+            // (b,d) pairs that can pass for some (a,c), kept in (b,d) order:
+            // log2 bound max_a S_ab + ||P_bd|| + max_c S_cd; the margin keeps it
+            // conservative against the FP32 rounding of the sums
+            int nk = 0;
+            for (int k0 = 0; k0 < nb * nd; k0 += 32) {
+                const int k = k0 + lane;
+                bool ok = false;
+                int ib = 0, id = 0;
+                if (k < nb * nd) {
+                    ib = fdiv(k, md);
+                    id = k - ib * nd;
+                    ok = !p.screen ||
+                         (tb.mb[ib] + tb.pbd[ib * STAGE + id] + tb.md[id] >= p.ltau - 2.f * LOG_MARGIN);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) tb.kl[nk + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(ib * STAGE + id);
+                nk += __popc(bal);
+            }
+            __syncwarp();
+            if (nk == 0) continue;
+            // sweep (row, k), row = (a,c), k = (b,d) in the compacted list,
+            // k fastest: one flat index so every lane has work
+            const int rows = na * nc;
+            const int total2 = rows * nk;
+            const Div dk(nk);
+            for (int base = 0; base < total2; base += 32) {
                 const unsigned idx = base + lane;
                 int stream = -1;
                 int32_t pab = -1, pcd = -1;
-                if (idx < (unsigned)total) {
-                    // (ia, ic, ib, id), id fastest
-                    const unsigned r1 = fdiv(idx, md);
-                    const int id = idx - r1 * nd;
-                    const unsigned r2 = fdiv(r1, mb);
-                    const int ib = r1 - r2 * nb;
-                    const unsigned ia = fdiv(r2, mc);
-                    const int ic = r2 - ia * nc;
-                    float x = 0.f;
-                    if (p.screen || p.mixed)
-                        x = tb.sab[ia * STAGE + ib] + tb.pbd[ib * STAGE + id] + tb.scd[ic * STAGE + id];
+                if (idx < (unsigned)total2) {
+                    const unsigned row = fdiv(idx, dk);
+                    const int k = idx - row * nk;
+                    const int ia = fdiv(row, mc);
+                    const int ic = row - ia * nc;
+                    const int bd = tb.kl[k];
+                    const int ib = bd >> 4, id = bd & 15;
+                    const float sab = tb.sab[ia * STAGE + ib], scd = tb.scd[ic * STAGE + id];
+                    const float x = sab + tb.pbd[ib * STAGE + id] + scd;
                     const int cls = tb.cab[ia * STAGE + ib] * 9 + tb.ccd[ic * STAGE + id];
-                    stream = decide(p, x, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, pab, pcd);
+                    stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, pab, pcd);
                 }
-                emit<WRITE>(stream, pab, pcd, lane, scount, ctr, rec, end, err);
+                emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
             }
         } else {
             // very large leaves: read the tables from global memory
@@ -184,21 +235,19 @@ k_expand(ExpandArgs p, unsigned long long* __restrict__ ctr, Quartet* __restrict
                     const int ic = r % nc;
                     const int ia = r / nc;
                     const int a = a0 + ia, b = b0 + ib, c = c0 + ic, d = d0 + id;
-                    float x = 0.f;
-                    if (p.screen || p.mixed)
-                        x = p.slog[(int64_t)a * p.ns + b] + p.plog[(int64_t)b * p.ns + d] +
-                            p.slog[(int64_t)c * p.ns + d];
+                    const float sab = p.slog[(int64_t)a * p.ns + b], scd = p.slog[(int64_t)c * p.ns + d];
+                    const float x = sab + p.plog[(int64_t)b * p.ns + d] + scd;
                     const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
-                    stream = decide(p, x, a, b, c, d, cls, pab, pcd);
+                    stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, pab, pcd);
                 }
-                emit<WRITE>(stream, pab, pcd, lane, scount, ctr, rec, end, err);
+                emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
             }
         }
     }
     if (!WRITE) {
         __syncthreads();
         for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x)
-            if (scount[i]) atomicAdd(ctr + i, (unsigned long long)scount[i]);
+            bin[(int64_t)i * gridDim.x + blockIdx.x] = scount[i];
         for (int d = 16; d > 0; d >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, d);
         if (lane == 0 && ncand) atomicAdd(cand, ncand / 32);
     }
@@ -232,21 +281,24 @@ static unsigned expand_grid(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
 }
 
+unsigned expand_blocks(int64_t n) { return expand_grid(n); }
+
 int expand_count(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed, int shell_screen,
-                 unsigned long long* d_count) {
+                 int64_t* bin) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<false><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, d_count, nullptr, c->d_counters + CTR_CAND, nullptr,
-                                                            nullptr);
+    k_expand<false><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+                                                                       nullptr, nullptr);
     return KX_OK;
 }
 
 int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed, int shell_screen,
-                 unsigned long long* d_cursor, Quartet* rec) {
+                 int64_t* bin_off, Quartet* rec) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<true><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, d_cursor, rec, nullptr, c->d_counters + CTR_END,
-                                                           c->d_counters + CTR_ERR);
+    k_expand<true><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
+                                                                      c->d_counters + CTR_END,
+                                                                      c->d_counters + CTR_ERR);
     return KX_OK;
 }
 

@@ -33,9 +33,7 @@ constexpr int BOYS_DENS = 32;
 constexpr double BOYS_TMAX = 40.0;
 constexpr int BOYS_NPTS = 40 * BOYS_DENS + 2;
 // layout of the small device counter array of a context
-constexpr int CTR_COUNT = 8;                       // per-stream record counts
-constexpr int CTR_CURSOR = CTR_COUNT + 2 * NCLASS; // per-stream write cursors
-constexpr int CTR_CAND = CTR_CURSOR + 2 * NCLASS;  // shell quartets screened
+constexpr int CTR_CAND = 8;                        // shell quartets screened
 constexpr int CTR_FILTER = CTR_CAND + 1;           // worklist export count
 constexpr int CTR_END = CTR_FILTER + 1;            // per-stream end offsets
 constexpr int CTR_ERR = CTR_END + 2 * NCLASS;      // write-guard violations
@@ -62,10 +60,17 @@ __host__ __device__ constexpr int etab(int la, int lb) { return (la + 1) * (lb +
 __host__ __device__ constexpr int eidx(int la, int lb, int i, int j, int t) {
     return (i * (lb + 1) + j) * (la + lb + 1) + t;
 }
-// pair record: p, Px, Py, Pz, prefactor, Ex[], Ey[], Ez[] (padded to even)
+// FP64 pair record: p, Px, Py, Pz, prefactor, Ex[], Ey[], Ez[] (padded to even)
 __host__ __device__ constexpr int pair_stride(int la, int lb) {
     return ((5 + 3 * etab(la, lb)) + 1) & ~1;
 }
+// FP32 pair record (64 bytes, four 16-byte loads): p, 1/(2p), prefactor,
+// P as hi+lo floats (so that P-Q keeps its digits when P ~ Q), P-A, P-B, pad.
+// The FP32 kernels rebuild the E coefficients from it in registers.
+constexpr int PAIR32_STRIDE = 16;
+enum { P32_P = 0, P32_INV2P = 1, P32_KAB = 2, P32_PHI = 3, P32_PLO = 6, P32_PA = 9, P32_PB = 12 };
+// row length of the FP32 Boys table (orders 0..BOYS_M, padded for 16-byte loads)
+constexpr int BOYS32_ROW = 16;
 
 // Shell pair metadata shared by the FP64 and FP32 pair tables.
 struct PairMeta {
@@ -174,6 +179,8 @@ struct kx_ctx {
     size_t scan_cap = 0;
     kx::Quartet* d_rec = nullptr;
     size_t rec_cap = 0;
+    int64_t* d_bin = nullptr;             // per (stream, block) counts and offsets
+    size_t bin_cap = 0;
     unsigned long long* d_counters = nullptr;   // small device counters
     kx::Task* d_keep = nullptr;                 // retained leaf worklist
     size_t keep_cap = 0, keep_n = 0;
@@ -250,10 +257,15 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
 struct ClassCounts {
     int64_t n[2 * NCLASS];     // [precision][class]; precision 0 = FP64
 };
+// Shell-screen passes over a list of leaf quartets.  expand_count writes
+// the number of kept quartets of every (stream, block) into bin[stream *
+// blocks + block] (blocks = expand_blocks(n)); after an exclusive scan of
+// bin, expand_write puts every record at its block's offset in its stream.
+unsigned expand_blocks(int64_t n_leaves);
 int expand_count(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
-                 int mixed, int shell_screen, unsigned long long* d_count);
+                 int mixed, int shell_screen, int64_t* bin);
 int expand_write(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
-                 int mixed, int shell_screen, unsigned long long* d_cursor, Quartet* rec);
+                 int mixed, int shell_screen, int64_t* bin_off, Quartet* rec);
 // launches the class kernel (la,lb,lc,ld) for n records; prec 0 = FP64, 1 = FP32
 // (prec 1 reads the FP32 copy of P, c->d_P32, leading dimension n_fn)
 int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,

@@ -703,14 +703,15 @@ __global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32, 
     #pragma unroll 1
     for (int m = 0; m <= M; ++m) {
         t64[(int64_t)i * (BOYS_M + 1) + m] = F[m];
-        t32[(int64_t)i * (BOYS_M + 1) + m] = (float)F[m];
+        t32[(int64_t)i * BOYS32_ROW + m] = (float)F[m];
     }
+    for (int m = M + 1; m < BOYS32_ROW; ++m) t32[(int64_t)i * BOYS32_ROW + m] = 0.f;
 }
 
 int boys_table(kx_ctx* c) {
     int npts = BOYS_NPTS;
     cudaError_t e = cudaMalloc(&c->d_boys64, sizeof(double) * npts * (BOYS_M + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_boys32, sizeof(float) * npts * (BOYS_M + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_boys32, sizeof(float) * npts * BOYS32_ROW);
     if (e != cudaSuccess) return cuda_check(c, e, "boys alloc");
     k_boys_table<<<(npts + 127) / 128, 128, 0, c->stream>>>(c->d_boys64, c->d_boys32, npts);
     return KX_OK;
@@ -721,9 +722,11 @@ int boys_table(kx_ctx* c) {
 // ===========================================================================
 
 // significant(a,b): the pair can appear in a surviving shell quartet.  With
-// the shell screen on, (S_ab * Pmax) * Smax <= tau implies every quartet
-// through (a,b) is culled (products of non-negative doubles are monotone).
-// Pairs emptied by Eq. 4 (s2 = 0) never take part.
+// the shell screen on, S_ab * Pmax * Smax <= tau implies every quartet
+// through (a,b) is culled; the test is made against tau * (1 - 2^-40) so
+// that the different rounding order of the quartet bound can never keep a
+// quartet whose pair was dropped.  Pairs emptied by Eq. 4 (s2 = 0) never
+// take part.
 __global__ void k_pair_flags(int ns, const int32_t* __restrict__ tl, const double* __restrict__ snorm,
                              const double* __restrict__ s2, double tau, double pmax, double smax, int screen,
                              int cls, int64_t* __restrict__ flag) {
@@ -731,7 +734,7 @@ __global__ void k_pair_flags(int ns, const int32_t* __restrict__ tl, const doubl
     if (i >= (int64_t)ns * ns) return;
     int a = (int)(i / ns), b = (int)(i % ns);
     int ok = (tl[a] * 3 + tl[b] == cls) && s2[i] > 0.0;
-    if (ok && screen) ok = __dmul_rn(__dmul_rn(snorm[i], pmax), smax) > tau;
+    if (ok && screen) ok = __dmul_rn(__dmul_rn(snorm[i], pmax), smax) > tau * (1.0 - 0x1p-40);
     flag[i] = ok;
 }
 
@@ -757,20 +760,28 @@ __global__ void k_pair_fill(int ns, int cls, const int32_t* __restrict__ tl, con
     double B[3] = {tctr[3 * b], tctr[3 * b + 1], tctr[3 * b + 2]};
     const int stride = pair_stride(la, lb), et = etab(la, lb);
     double* o = d64 + s * stride;
-    float* o32 = d32 + s * stride;
+    float* o32 = d32 + s * PAIR32_STRIDE;
     double AB2 = 0.0;
     double E[45];
     o[0] = p;
+    o32[P32_P] = (float)p;
+    o32[P32_INV2P] = (float)(0.5 / p);
     for (int x = 0; x < 3; ++x) {
         double Px = (al * A[x] + be * B[x]) / p;
         o[1 + x] = Px;
+        const float hi = (float)Px;
+        o32[P32_PHI + x] = hi;
+        o32[P32_PLO + x] = (float)(Px - (double)hi);
+        o32[P32_PA + x] = (float)(Px - A[x]);
+        o32[P32_PB + x] = (float)(Px - B[x]);
         AB2 += (A[x] - B[x]) * (A[x] - B[x]);
         hermite_e_1d(la, lb, Px - A[x], Px - B[x], 0.5 / p, E);
         for (int k = 0; k < et; ++k) o[5 + x * et + k] = E[k];
     }
     o[4] = norm_prim(al, la) * norm_prim(be, lb) * exp(-al * be / p * AB2);
+    o32[P32_KAB] = (float)o[4];
+    o32[15] = 0.f;
     if (stride > 5 + 3 * et) o[stride - 1] = 0.0;
-    for (int k = 0; k < stride; ++k) o32[k] = (float)o[k];
 }
 
 __global__ void k_max_reduce(const double* __restrict__ x, int64_t n, unsigned long long* __restrict__ out) {
@@ -816,7 +827,7 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
             size_t cap = need + need / 8 + 16;
             int stride = pair_stride(la, lb);
             cudaError_t e = cudaMalloc(&c->d_pair64[cls], sizeof(double) * stride * cap);
-            if (e == cudaSuccess) e = cudaMalloc(&c->d_pair32[cls], sizeof(float) * stride * cap);
+            if (e == cudaSuccess) e = cudaMalloc(&c->d_pair32[cls], sizeof(float) * PAIR32_STRIDE * cap);
             if (e == cudaSuccess) e = cudaMalloc(&c->d_pairmeta[cls], sizeof(PairMeta) * cap);
             if (e != cudaSuccess) {
                 c->pair_cap[cls] = 0;

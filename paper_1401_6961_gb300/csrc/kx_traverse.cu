@@ -257,16 +257,16 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     if (n <= 0) return KX_OK;
     const int mixed = r.o->precision == KX_MIXED;
     const double split = mixed ? r.o->split_threshold : 0.0;
-    unsigned long long* cnt = c->d_counters + CTR_COUNT;
     r.tm->mark(ST_EXPAND);
-    KX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * NCLASS, c->stream));
-    KX_TRY(expand_count(c, leaves, n, r.o->tau, split, mixed, r.o->shell_screen, cnt));
+    const unsigned nb = expand_blocks(n);
+    const int64_t nbin = (int64_t)2 * NCLASS * nb;
+    KX_TRY(grow(c, &c->d_bin, &c->bin_cap, (size_t)(2 * nbin)));
+    int64_t* bin = c->d_bin;
+    int64_t* binoff = c->d_bin + nbin;
+    KX_TRY(expand_count(c, leaves, n, r.o->tau, split, mixed, r.o->shell_screen, bin));
     c->launches++;
-    unsigned long long h[2 * NCLASS];
-    KX_CUDA(c, cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    KX_CUDA(c, cudaStreamSynchronize(c->stream));
     int64_t total = 0;
-    for (int s = 0; s < 2 * NCLASS; ++s) total += (int64_t)h[s];
+    KX_TRY(exclusive_scan(c, bin, binoff, nbin, &total));
     if (total > r.rec_limit && n > 1) {
         // too many records for one pass: halve the leaf list
         int64_t h0 = n / 2;
@@ -274,19 +274,20 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
         return process_leaves(r, leaves + h0, n - h0);
     }
     if (total == 0) return KX_OK;
-    KX_TRY(grow(c, &c->d_rec, &c->rec_cap, (size_t)total));
-    unsigned long long cur[2 * NCLASS], endv[2 * NCLASS];
+    // stream s starts at binoff[s * nb]
     int64_t off[2 * NCLASS + 1];
-    off[0] = 0;
+    KX_CUDA(c, cudaMemcpy2DAsync(off, sizeof(int64_t), binoff, sizeof(int64_t) * nb, sizeof(int64_t), 2 * NCLASS,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    off[2 * NCLASS] = total;
+    unsigned long long h[2 * NCLASS], endv[2 * NCLASS];
     for (int s = 0; s < 2 * NCLASS; ++s) {
-        cur[s] = (unsigned long long)off[s];
-        off[s + 1] = off[s] + (int64_t)h[s];
+        h[s] = (unsigned long long)(off[s + 1] - off[s]);
         endv[s] = (unsigned long long)off[s + 1];
     }
-    unsigned long long* cursor = c->d_counters + CTR_CURSOR;
-    KX_CUDA(c, cudaMemcpyAsync(cursor, cur, sizeof(cur), cudaMemcpyHostToDevice, c->stream));
+    KX_TRY(grow(c, &c->d_rec, &c->rec_cap, (size_t)total));
     KX_CUDA(c, cudaMemcpyAsync(c->d_counters + CTR_END, endv, sizeof(endv), cudaMemcpyHostToDevice, c->stream));
-    KX_TRY(expand_write(c, leaves, n, r.o->tau, split, mixed, r.o->shell_screen, cursor, c->d_rec));
+    KX_TRY(expand_write(c, leaves, n, r.o->tau, split, mixed, r.o->shell_screen, binoff, c->d_rec));
     c->launches++;
     r.tm->mark(ST_ERI);
     for (int s = 0; s < 2 * NCLASS; ++s) {
@@ -348,6 +349,7 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
     cudaMemGetInfo(&fr, &tot);
     int64_t lim = (int64_t)std::min<size_t>((size_t)1 << 30, fr / 4 / sizeof(Quartet));
     r.rec_limit = o->chunk_records > 0 ? o->chunk_records : std::max<int64_t>(lim, 1 << 20);
+    r.rec_limit = std::min<int64_t>(r.rec_limit, (int64_t)1 << 31);   // record slots are 32-bit in the binning
     const int64_t lq_cap = std::max<int64_t>(r.rec_limit / 48, 1 << 16);
 
     c->launches = 0;
