@@ -146,10 +146,11 @@ int kx_get_leaves(const kx_ctx* c, int32_t* lo, int32_t* hi, int32_t cap,
                   int32_t* n_leaf, int32_t* depth);
 
 /* Leaf quartets (A,B,C,D) kept by the last kx_exchange that had
- * keep_worklist = 1, as leaf ordinals, into host out[cap][4].  With
+ * keep_worklist = 1 (or by kx_traverse / kx_cull_kept), as leaf ordinals, into host out[cap][4].  With
  * n_filter > 0 only quartets whose A is in a_filter[] are returned.
  * *n = number matching (entries beyond cap are not written; KX_ECAPACITY
- * then).  Order is unspecified. */
+ * then).  Without a filter the list comes in kept order (the order of
+ * kx_leaf_features); with one the order is unspecified. */
 int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter,
                     int32_t* out, int64_t cap, int64_t* n);
 
@@ -171,6 +172,74 @@ int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32
  * KX_FP64 or KX_MIXED (= FP32).  *gflops = measured GFLOP/s (2 per FMA).
  * Not part of the exchange build; used to state roofline fractions. */
 int kx_peak_probe(int device, int precision, double* gflops);
+
+/* ------------------------------------------------------------------------
+ * Learned culling (a growth direction beyond the paper).  A small network
+ * predicts, from ten descriptors of a leaf quartet, log10 of the Frobenius
+ * norm of its contribution to K; a leaf quartet whose exact Eq. 8 bound is
+ * at most 10 tau is dropped when the predicted contributions of such
+ * quartets fit a per-K-block budget (kx_cull_kept), so any quartet whose
+ * bound exceeds 10 tau is always evaluated.  The pieces
+ * below compose: kx_traverse -> kx_leaf_features -> kx_mlp_infer_bf16 ->
+ * kx_cull_kept -> kx_evaluate_kept.
+ * ------------------------------------------------------------------------ */
+#define KX_NFEAT 10
+#define KX_MLP_HIDDEN 64
+/* parameters (FP32): mu[10], 1/sigma[10], W1[64][10], b1[64], W2[64][64],
+ * b2[64], W3[64][64], b3[64], W4[64], b4 */
+#define KX_MLP_NPARAM 9109
+
+/* The traversal of kx_exchange (Eqs. 7-8) without the ERI stage: computes
+ * the P norms of P (device) and keeps every surviving leaf quartet on the
+ * device; *n_leaves = their number. */
+int kx_traverse(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, int64_t* n_leaves);
+
+/* Descriptors of the kept leaf quartets (A,B,C,D), in kept order, into the
+ * DEVICE array feat[n][10] (FP32): log10 ||Q_AB||, log10 ||Q_CD||,
+ * log10 ||P_BD||, log10 beta, |c_A - c_C|, |c_B - c_D|, distance between
+ * the bra and ket centroids (bohr), largest block radius, largest l, log10
+ * of the smallest exponent.  *n = kept count (KX_ECAPACITY if > cap). */
+int kx_leaf_features(kx_ctx* c, float* feat, int64_t cap, int64_t* n);
+
+/* Drops kept leaf quartet i = (A,B,C,D) when its bound is at most 10 tau
+ * and pred[i] + log10(m_AC)/2 < log10_budget, m_AC being the number of kept
+ * quartets of bound <= 10 tau that share its K block (A,C): the predicted
+ * root-sum-square of what any K block loses stays below the budget.  pred: DEVICE
+ * array in kept order (log10 contributions, any safety margin added by the
+ * caller).  Keeps the order of the rest; *n_kept = what remains. */
+int kx_cull_kept(kx_ctx* c, const float* pred, double tau, double log10_budget, int64_t* n_kept);
+
+/* The ERI stage (shell screen, class kernels, K accumulation) over the kept
+ * leaf quartets; P and K device, K overwritten. */
+int kx_evaluate_kept(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+                     kx_stats* st);
+
+/* The ERI stage over an explicit list of leaf quartets (host int32[n][4],
+ * leaf ordinals).  For a list whose (A,C) are pairwise distinct every
+ * quartet owns its K block, so kx_block_norms then returns the exact norm
+ * of each quartet's contribution (the training targets). */
+int kx_exchange_leaves(kx_ctx* c, const double* P, int64_t ldp, const int32_t* leaves, int64_t n,
+                       const kx_opts* o, double* K, int64_t ldk, kx_stats* st);
+
+/* ||K_AC||_F for every leaf quartet of leaves (host int32[n][4]) from the
+ * DEVICE matrix K; norms host double[n]. */
+int kx_block_norms(kx_ctx* c, const double* K, int64_t ldk, const int32_t* leaves, int64_t n,
+                   double* norms);
+
+/* MLP inference with BF16 weights and activations and FP32 accumulation:
+ * pred[i] for the n feature rows (DEVICE arrays), on `stream`. */
+int kx_mlp_infer_bf16(const float* params, const float* feat, int64_t n, float* pred, void* stream);
+
+/* Loss 0.5 * mean((y - target)^2) over the n rows and its gradient with
+ * respect to every trained parameter (FP32, DEVICE arrays; the two
+ * normalisation vectors get zero gradient); *loss on the host. */
+int kx_mlp_loss_grad(const float* params, const float* feat, const float* target, int64_t n,
+                     float* grad, double* loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with
+ * `step` >= 1) on the trained parameters; m and v are DEVICE state. */
+int kx_mlp_adam(float* params, const float* grad, float* m, float* v, float lr, int32_t step,
+                void* stream);
 
 /* Largest frontier, in tasks, that kx_traverse_level_noalloc accepts. */
 #define KX_NOALLOC_MAX_TASKS (1 << 18)

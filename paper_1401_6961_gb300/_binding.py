@@ -23,7 +23,12 @@ ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "K
 EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
            "kx_exchange_host", "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
+           "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
+           "kx_block_norms", "kx_mlp_infer_bf16", "kx_mlp_loss_grad", "kx_mlp_adam",
            "kx_last_error", "kx_destroy"]
+KX_NFEAT = 10
+KX_MLP_HIDDEN = 64
+KX_MLP_NPARAM = 9109
 KX_NOALLOC_MAX_TASKS = 1 << 18
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -101,6 +106,17 @@ def load() -> ctypes.CDLL:
     L.kx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _f64p]
     L.kx_traverse_level_noalloc.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_double, vp,
                                             ctypes.c_int64, _i64p]
+    L.kx_traverse.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), _i64p]
+    L.kx_leaf_features.argtypes = [vp, vp, ctypes.c_int64, _i64p]
+    L.kx_cull_kept.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, _i64p]
+    L.kx_evaluate_kept.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), vp, ctypes.c_int64,
+                                   ctypes.POINTER(kx_stats)]
+    L.kx_exchange_leaves.argtypes = [vp, vp, ctypes.c_int64, _i32p, ctypes.c_int64, ctypes.POINTER(kx_opts), vp,
+                                     ctypes.c_int64, ctypes.POINTER(kx_stats)]
+    L.kx_block_norms.argtypes = [vp, vp, ctypes.c_int64, _i32p, ctypes.c_int64, _f64p]
+    L.kx_mlp_infer_bf16.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    L.kx_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, vp, _f64p, vp]
+    L.kx_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int32, vp]
     L.kx_last_error.argtypes = [vp]
     L.kx_last_error.restype = ctypes.c_char_p
     L.kx_destroy.argtypes = [vp]
@@ -254,6 +270,76 @@ def kx_traverse_level_noalloc(ctx, level: int, front_ptr: int, n: int, tau: floa
     _check(ctx, load().kx_traverse_level_noalloc(ctx, int(level), ctypes.c_void_p(front_ptr), int(n), float(tau),
                                                  ctypes.c_void_p(next_ptr), int(cap), ctypes.byref(nn)))
     return int(nn.value)
+
+
+# --- learned culling ------------------------------------------------------
+
+def kx_traverse(ctx, P_ptr: int, ldp: int, opts: kx_opts) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load().kx_traverse(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts), ctypes.byref(n)))
+    return int(n.value)
+
+
+def kx_leaf_features(ctx, feat_ptr: int, cap: int) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load().kx_leaf_features(ctx, ctypes.c_void_p(feat_ptr), int(cap), ctypes.byref(n)))
+    return int(n.value)
+
+
+def kx_cull_kept(ctx, pred_ptr: int, tau: float, log10_budget: float) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load().kx_cull_kept(ctx, ctypes.c_void_p(pred_ptr), float(tau), float(log10_budget),
+                                    ctypes.byref(n)))
+    return int(n.value)
+
+
+def kx_evaluate_kept(ctx, P_ptr: int, ldp: int, opts: kx_opts, K_ptr: int, ldk: int) -> kx_stats:
+    st = kx_stats()
+    _check(ctx, load().kx_evaluate_kept(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts),
+                                        ctypes.c_void_p(K_ptr), int(ldk), ctypes.byref(st)))
+    return st
+
+
+def kx_exchange_leaves(ctx, P_ptr: int, ldp: int, leaves: np.ndarray, opts: kx_opts, K_ptr: int,
+                       ldk: int) -> kx_stats:
+    lv = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1, 4)
+    st = kx_stats()
+    _check(ctx, load().kx_exchange_leaves(ctx, ctypes.c_void_p(P_ptr), int(ldp), _p(lv, _i32p), int(lv.shape[0]),
+                                          ctypes.byref(opts), ctypes.c_void_p(K_ptr), int(ldk), ctypes.byref(st)))
+    return st
+
+
+def kx_block_norms(ctx, K_ptr: int, ldk: int, leaves: np.ndarray) -> np.ndarray:
+    lv = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1, 4)
+    out = np.zeros(lv.shape[0])
+    _check(ctx, load().kx_block_norms(ctx, ctypes.c_void_p(K_ptr), int(ldk), _p(lv, _i32p), int(lv.shape[0]),
+                                      _p(out, _f64p)))
+    return out
+
+
+def _rc(r: int, what: str):
+    if r != KX_OK:
+        raise KxError(r, what)
+
+
+def kx_mlp_infer_bf16(params_ptr: int, feat_ptr: int, n: int, pred_ptr: int, stream: int = 0) -> None:
+    _rc(load().kx_mlp_infer_bf16(ctypes.c_void_p(params_ptr), ctypes.c_void_p(feat_ptr), int(n),
+                                 ctypes.c_void_p(pred_ptr), ctypes.c_void_p(int(stream))), "kx_mlp_infer_bf16")
+
+
+def kx_mlp_loss_grad(params_ptr: int, feat_ptr: int, target_ptr: int, n: int, grad_ptr: int,
+                     stream: int = 0) -> float:
+    loss = ctypes.c_double()
+    _rc(load().kx_mlp_loss_grad(ctypes.c_void_p(params_ptr), ctypes.c_void_p(feat_ptr), ctypes.c_void_p(target_ptr),
+                                int(n), ctypes.c_void_p(grad_ptr), ctypes.byref(loss), ctypes.c_void_p(int(stream))),
+        "kx_mlp_loss_grad")
+    return float(loss.value)
+
+
+def kx_mlp_adam(params_ptr: int, grad_ptr: int, m_ptr: int, v_ptr: int, lr: float, step: int,
+                stream: int = 0) -> None:
+    _rc(load().kx_mlp_adam(ctypes.c_void_p(params_ptr), ctypes.c_void_p(grad_ptr), ctypes.c_void_p(m_ptr),
+                           ctypes.c_void_p(v_ptr), float(lr), int(step), ctypes.c_void_p(int(stream))), "kx_mlp_adam")
 
 
 def kx_last_error(ctx) -> str:

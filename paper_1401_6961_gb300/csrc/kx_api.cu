@@ -47,7 +47,7 @@ void free_all(kx_ctx* c) {
                     c->d_node_nchild, c->d_sq_s, c->d_sq_p, c->d_nrm_s, c->d_nrm_p, c->d_leaf_lo, c->d_leaf_hi,
                     c->d_boys64, c->d_boys32, c->d_pairmap, c->d_scratch, c->d_front[0], c->d_front[1],
                     c->d_mask, c->d_scan, c->d_rec, c->d_bin, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
-                    c->d_hostP, c->d_hostK};
+                    c->d_hostP, c->d_hostK, c->d_leafdesc, c->d_list};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < NPAIRCLASS; ++i) {
@@ -266,12 +266,19 @@ int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter, int32_
     if (e == cudaSuccess && cap > 0) e = cudaMalloc(&d_out, sizeof(Task) * cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
     unsigned long long cnt = 0;
-    if (e == cudaSuccess && c->keep_n > 0) {
+    if (n_filter == 0) {
+        // the whole list, in kept order
+        cnt = (unsigned long long)c->keep_n;
+        const int64_t m = std::min<int64_t>((int64_t)cnt, cap);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync(d_out, c->d_keep, sizeof(Task) * m, cudaMemcpyDeviceToDevice, c->stream);
+    } else if (e == cudaSuccess && c->keep_n > 0) {
         unsigned grid = (unsigned)std::min<size_t>((c->keep_n + 255) / 256, 152 * 32);
         k_filter_work<<<grid, 256, 0, c->stream>>>(c->d_keep, (int64_t)c->keep_n, d_mark, d_out, d_cnt, cap);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && n_filter > 0)
+        e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) {
         *n = (int64_t)cnt;

@@ -199,6 +199,11 @@ struct kx_ctx {
     size_t host_cap = 0;
 
     double tau_ovlp = 0.0;
+    double kept_tau = 0.0;                // tau of the traversal that made the kept list
+    float* d_leafdesc = nullptr;          // per-leaf centroid, radius, max l, min exponent
+    size_t leafdesc_cap = 0;
+    kx::Task* d_list = nullptr;           // explicit leaf lists and compaction scratch
+    size_t list_cap = 0;
     bool have_pq = false;
     int64_t launches = 0;                 // kernels launched by the current build
     // per-stream profile of the last profiled build
@@ -252,6 +257,11 @@ int pair_tables(kx_ctx* c, double tau, bool want32);          // kx_setup.cu
 int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);  // kx_traverse.cu
 int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
                           double* K, int64_t ldk, kx_stats* st);  // kx_traverse.cu
+// what one driver call does: the whole build, the traversal alone (the leaf
+// list is kept), or the ERI stage over an explicit device leaf list
+enum { RUN_EXCHANGE = 0, RUN_TRAVERSE = 1, RUN_EVALUATE = 2 };
+int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+          kx_stats* st, const Task* list, int64_t nlist);
 
 // shell expansion + class kernels (kx_expand.cu, kx_eri_*.cu)
 struct ClassCounts {

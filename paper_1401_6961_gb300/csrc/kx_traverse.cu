@@ -250,6 +250,7 @@ struct Run {
 };
 
 int process_leaves(Run& r, const Task* leaves, int64_t n);
+int finish_run(kx_ctx* c, kx_stats* st, Timer& tm, int D);
 
 // shell screen, class binning and class kernels for one list of leaf quartets
 int process_leaves(Run& r, const Task* leaves, int64_t n) {
@@ -338,9 +339,10 @@ int keep_leaves(kx_ctx* c, const Task* leaves, int64_t n) {
 
 }  // namespace
 
-int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
-                          kx_stats* st) {
+int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+          kx_stats* st, const Task* list, int64_t nlist) {
     const int D = c->depth;
+    const bool evaluate = mode != RUN_TRAVERSE;
     Timer tm{c, {}};
     Run r{c, P, ldp, o, K, ldk, st, &tm, 0, 0.0};
     // record budget per pass: the caller's, else 2^30 records (8 GB) or a
@@ -365,16 +367,27 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
     }
     c->prof_ev.clear();
     tm.mark(ST_NORMS);
-    KX_CUDA(c, cudaMemset2DAsync(K, sizeof(double) * ldk, 0, sizeof(double) * c->n_fn, c->n_fn, c->stream));
+    if (evaluate)
+        KX_CUDA(c, cudaMemset2DAsync(K, sizeof(double) * ldk, 0, sizeof(double) * c->n_fn, c->n_fn, c->stream));
     KX_TRY(p_norms(c, P, ldp));
-    if (o->precision == KX_MIXED) {
+    if (evaluate && o->precision == KX_MIXED) {
         KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)c->n_fn * c->n_fn));
         k_to_f32<<<1024, 256, 0, c->stream>>>(P, ldp, c->n_fn, c->d_P32);
         c->launches++;
     }
-    KX_TRY(pair_tables(c, o->tau, o->shell_screen != 0));
-    c->keep_n = 0;
-    c->keep_valid = false;
+    if (evaluate) KX_TRY(pair_tables(c, o->tau, o->shell_screen != 0));
+    const bool keep = mode == RUN_TRAVERSE || (mode == RUN_EXCHANGE && o->keep_worklist);
+    if (mode != RUN_EVALUATE) {
+        c->keep_n = 0;
+        c->keep_valid = false;
+    }
+    if (mode == RUN_EVALUATE) {
+        // an explicit leaf-quartet list: the ERI stage in chunks of lq_cap
+        st->n_leaf_quartets = nlist;
+        for (int64_t i0 = 0; i0 < nlist; i0 += lq_cap)
+            KX_TRY(process_leaves(r, list + i0, std::min<int64_t>(lq_cap, nlist - i0)));
+        return finish_run(c, st, tm, D);
+    }
 
     tm.mark(ST_TRAV);
     const double* S = c->d_nrm_s;
@@ -396,8 +409,8 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
         KX_CUDA(c, cudaStreamSynchronize(c->stream));
         st->n_tasks[0] = nk;
         st->n_leaf_quartets = nk;
-        if (o->keep_worklist) KX_TRY(keep_leaves(c, c->d_front[0], nk));
-        KX_TRY(process_leaves(r, c->d_front[0], nk));
+        if (keep) KX_TRY(keep_leaves(c, c->d_front[0], nk));
+        if (evaluate) KX_TRY(process_leaves(r, c->d_front[0], nk));
     } else {
         for (int k = 0; k < D; ++k) {
             const int nn = c->levels[k + 1].n;
@@ -456,12 +469,18 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
                 k_expand_write<<<g2, 256, 0, c->stream>>>(c->d_front[cur], p0, p1, c->d_mask, off, o0, child,
                                                           c->d_front[1 - cur]);
                 c->launches++;
-                if (o->keep_worklist) KX_TRY(keep_leaves(c, c->d_front[1 - cur], o1 - o0));
-                KX_TRY(process_leaves(r, c->d_front[1 - cur], o1 - o0));
+                if (keep) KX_TRY(keep_leaves(c, c->d_front[1 - cur], o1 - o0));
+                if (evaluate) KX_TRY(process_leaves(r, c->d_front[1 - cur], o1 - o0));
             }
         }
     }
-    if (o->keep_worklist) c->keep_valid = true;
+    if (keep) c->keep_valid = true;
+    return finish_run(c, st, tm, D);
+}
+
+namespace {
+
+int finish_run(kx_ctx* c, kx_stats* st, Timer& tm, int D) {
     tm.mark(ST_NONE);
     KX_CUDA(c, cudaStreamSynchronize(c->stream));
     KX_CUDA(c, cudaGetLastError());
@@ -490,6 +509,13 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
     st->n_candidates = (int64_t)cand;
     if (werr) return set_err(c, KX_ECUDA, "shell-quartet count and write passes disagree");
     return KX_OK;
+}
+
+}  // namespace
+
+int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+                          kx_stats* st) {
+    return drive(c, RUN_EXCHANGE, P, ldp, o, K, ldk, st, nullptr, 0);
 }
 
 }  // namespace kx
