@@ -58,7 +58,7 @@ typedef struct kx_ctx kx_ctx;          /* opaque, owned by the library */
 /* Molecule and shell list (host memory, copied by kx_create). */
 typedef struct {
     int32_t n_atom;
-    int32_t n_shell;             /* 1 .. 65535 */
+    int32_t n_shell;             /* 1 .. 65535 (per system) */
     const double* xyz;           /* [n_atom][3] atom centres, bohr */
     const int32_t* shell_atom;   /* [n_shell] atom of each shell */
     const int32_t* shell_l;      /* [n_shell] angular momentum, 0..2 */
@@ -118,14 +118,17 @@ int kx_build_schwarz(kx_ctx* c, double tau_ovlp);
  * leaf_max_functions functions (a single shell is always a leaf; the paper
  * uses 10), and the Schwarz norm pyramid over it (Eq. 2).  perm, if not
  * NULL, is a host array [n_shell] giving the user shell at each tree
- * position and replaces the Hilbert order.  Requires kx_build_schwarz. */
+ * position and replaces the Hilbert order (in a batch it must map every
+ * system's range of positions onto that system's shells).  Requires
+ * kx_build_schwarz. */
 int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm);
 
 /* One exchange build (Eqs. 6-8).  P and K are DEVICE pointers to row-major
  * FP64 matrices of n_fn x n_fn in user function order with leading
  * dimensions ldp, ldk >= n_fn; the caller owns both.  K is overwritten.  P
  * need not be symmetric.  st may be NULL.  Asynchronous on the context's
- * stream except for a few small size read-backs. */
+ * stream except for a few small size read-backs.  Single-system contexts
+ * only (KX_EINVAL on a batch: see kx_exchange_batch). */
 int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
                 double* K, int64_t ldk, kx_stats* st);
 
@@ -134,7 +137,41 @@ int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
 int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts* o,
                      double* K_host, int64_t ldk, kx_stats* st);
 
-/* Number of basis functions. */
+/* ------------------------------------------------------------------------
+ * Batches of independent systems (a growth direction beyond the paper: many
+ * uneven systems in one traversal and one set of class-kernel launches).
+ * The systems are concatenated in input order: atoms, shells and functions
+ * of system y follow those of systems 0..y-1, and the tree positions of
+ * system y form the range of its shells.  Every system gets its own Hilbert
+ * order (Sec. "Exchange as hextree traversal") and its own bisection tree
+ * (Eq. 1); level k of the forest holds the level-k nodes of every system,
+ * system-major, so kx_get_leaves and kx_get_worklist report leaf ordinals of
+ * the forest.  A task never mixes systems: the level-0 tasks are (Y,Y,Y,Y),
+ * one per system Y, and children stay inside their parent's system.
+ * ------------------------------------------------------------------------ */
+
+/* Creates a context holding n_sys (1..65535) systems bases[0..n_sys-1]
+ * (host; each as for kx_create).  kx_build_schwarz and kx_build_tree then
+ * apply to every system.  kx_create(out, b, ...) is
+ * kx_create_batch(out, 1, b, ...). */
+int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int device, void* cuda_stream);
+
+/* One exchange build of every system of the batch (Eqs. 6-8 per system).
+ * P and K are DEVICE arrays of kx_packed_size(c) doubles: system y's
+ * n_y x n_y matrix (row-major, its own user function order) starts at
+ * sum_{z<y} n_z^2.  K is overwritten.  Works on single-system contexts
+ * too (packed = dense n_fn x n_fn). */
+int kx_exchange_batch(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st);
+
+/* kx_exchange_batch with HOST buffers (copies inside, returns when K is on
+ * the host). */
+int kx_exchange_batch_host(kx_ctx* c, const double* P_host, const kx_opts* o, double* K_host,
+                           kx_stats* st);
+
+/* Doubles of a packed P or K: sum over the systems of n_y^2. */
+int64_t kx_packed_size(const kx_ctx* c);
+
+/* Number of basis functions (summed over the systems of a batch). */
 int64_t kx_n_functions(const kx_ctx* c);
 
 /* Tree order: perm[i] = user shell at tree position i (host array). */
@@ -157,7 +194,9 @@ int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter,
 /* Shell-level tables in USER shell order (host arrays [n_shell][n_shell]):
  * s2 = squared Schwarz norms (after any Eq. 4 prune), pq = squared
  * Frobenius norms of the P shell blocks of the last kx_exchange (may be
- * NULL). */
+ * NULL).  For a batch: one dense block per system, system y's
+ * [n_shell_y][n_shell_y] block (its own user shell order) starting at
+ * sum_{z<y} n_shell_z^2. */
 int kx_get_norms(kx_ctx* c, double* s2, double* pq);
 
 /* Per-stream totals of the last kx_exchange run with profile = 1, for the
@@ -181,7 +220,9 @@ int kx_peak_probe(int device, int precision, double* gflops);
  * quartets fit a per-K-block budget (kx_cull_kept), so any quartet whose
  * bound exceeds 10 tau is always evaluated.  The pieces
  * below compose: kx_traverse -> kx_leaf_features -> kx_mlp_infer_bf16 ->
- * kx_cull_kept -> kx_evaluate_kept.
+ * kx_cull_kept -> kx_evaluate_kept.  The context-bound calls of this block
+ * (and kx_traverse_level_noalloc) take single-system contexts; on a batch
+ * they return KX_ENOTIMPL.
  * ------------------------------------------------------------------------ */
 #define KX_NFEAT 10
 #define KX_MLP_HIDDEN 64

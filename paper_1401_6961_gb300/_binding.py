@@ -21,7 +21,8 @@ ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "K
 
 # every entry point declared in include/kx.h
 EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
-           "kx_exchange_host", "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
+           "kx_exchange_host", "kx_create_batch", "kx_exchange_batch", "kx_exchange_batch_host",
+           "kx_packed_size", "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
            "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
            "kx_block_norms", "kx_mlp_infer_bf16", "kx_mlp_loss_grad", "kx_mlp_adam",
@@ -96,6 +97,11 @@ def load() -> ctypes.CDLL:
                               ctypes.POINTER(kx_stats)]
     L.kx_exchange_host.argtypes = [vp, _f64p, ctypes.c_int64, ctypes.POINTER(kx_opts), _f64p,
                                    ctypes.c_int64, ctypes.POINTER(kx_stats)]
+    L.kx_create_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(kx_basis), ctypes.c_int, vp]
+    L.kx_exchange_batch.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.POINTER(kx_stats)]
+    L.kx_exchange_batch_host.argtypes = [vp, _f64p, ctypes.POINTER(kx_opts), _f64p, ctypes.POINTER(kx_stats)]
+    L.kx_packed_size.argtypes = [vp]
+    L.kx_packed_size.restype = ctypes.c_int64
     L.kx_n_functions.argtypes = [vp]
     L.kx_n_functions.restype = ctypes.c_int64
     L.kx_get_order.argtypes = [vp, _i32p]
@@ -122,7 +128,7 @@ def load() -> ctypes.CDLL:
     L.kx_destroy.argtypes = [vp]
     L.kx_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("kx_default_opts", "kx_n_functions", "kx_last_error", "kx_destroy"):
+        if name not in ("kx_default_opts", "kx_n_functions", "kx_packed_size", "kx_last_error", "kx_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -168,6 +174,37 @@ def kx_create(xyz, shell_atom, shell_l, shell_alpha, device: int = 0, stream: in
     if r != KX_OK:
         raise KxError(r, "kx_create failed")
     return ctx
+
+
+def kx_create_batch(systems, device: int = 0, stream: int = 0) -> ctypes.c_void_p:
+    """Context for a batch of systems (each with xyz, shell_atom, shell_l, shell_alpha)."""
+    arrs = [_BasisArrays(s.xyz, s.shell_atom, s.shell_l, s.shell_alpha) for s in systems]
+    bases = (kx_basis * len(arrs))(*[a.s for a in arrs])
+    ctx = ctypes.c_void_p()
+    r = load().kx_create_batch(ctypes.byref(ctx), len(arrs), bases, int(device), ctypes.c_void_p(int(stream)))
+    if r != KX_OK:
+        raise KxError(r, "kx_create_batch failed")
+    return ctx
+
+
+def kx_exchange_batch(ctx, P_ptr: int, opts: kx_opts, K_ptr: int) -> kx_stats:
+    """Device pointers (ints) to packed FP64 P and K (kx_packed_size doubles)."""
+    st = kx_stats()
+    _check(ctx, load().kx_exchange_batch(ctx, ctypes.c_void_p(P_ptr), ctypes.byref(opts), ctypes.c_void_p(K_ptr),
+                                         ctypes.byref(st)))
+    return st
+
+
+def kx_exchange_batch_host(ctx, P: np.ndarray, opts: kx_opts, K: np.ndarray) -> kx_stats:
+    assert P.dtype == np.float64 and K.dtype == np.float64 and P.flags["C_CONTIGUOUS"] and K.flags["C_CONTIGUOUS"]
+    st = kx_stats()
+    _check(ctx, load().kx_exchange_batch_host(ctx, P.ctypes.data_as(_f64p), ctypes.byref(opts),
+                                              K.ctypes.data_as(_f64p), ctypes.byref(st)))
+    return st
+
+
+def kx_packed_size(ctx) -> int:
+    return int(load().kx_packed_size(ctx))
 
 
 def kx_build_schwarz(ctx, tau_ovlp: float = 0.0) -> None:
@@ -235,9 +272,12 @@ def kx_get_worklist(ctx, a_filter: Optional[Sequence[int]] = None, cap: int = 1 
         return out[: n.value].copy()
 
 
-def kx_get_norms(ctx, n_shell: int, with_p: bool = True) -> Tuple[np.ndarray, Optional[np.ndarray]]:
-    s2 = np.zeros((n_shell, n_shell))
-    pq = np.zeros((n_shell, n_shell)) if with_p else None
+def kx_get_norms(ctx, n_shell: int, with_p: bool = True, total: Optional[int] = None):
+    """Dense [n_shell, n_shell] tables; for a batch pass ``total`` (sum of
+    n_shell_y^2) to get the flat per-system blocks."""
+    shape = (n_shell, n_shell) if total is None else (int(total),)
+    s2 = np.zeros(shape)
+    pq = np.zeros(shape) if with_p else None
     _check(ctx, load().kx_get_norms(ctx, _p(s2, _f64p), _p(pq, _f64p) if with_p else None))
     return s2, pq
 
@@ -412,5 +452,66 @@ class Exchange:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class BatchExchange:
+    """A context for a batch of independent systems:
+    ``BatchExchange(systems)(P) -> K`` with P and K packed (system y's
+    n_y x n_y matrix at ``offsets[y]``, row-major) in 1-D float64 device
+    tensors of ``size`` entries."""
+
+    def __init__(self, systems, device: int = 0, leaf_max: int = 10, tau_ovlp: float = 0.0, stream=None):
+        import torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.n_sys = len(systems)
+        self.n_shell = [int(len(s.shell_l)) for s in systems]
+        self.n_fn = [int(sum((l + 1) * (l + 2) // 2 for l in np.asarray(s.shell_l))) for s in systems]
+        self.offsets = np.concatenate([[0], np.cumsum(np.asarray(self.n_fn, dtype=np.int64) ** 2)])
+        self.shell_offsets = np.concatenate([[0], np.cumsum(self.n_shell)])
+        self.ctx = kx_create_batch(systems, device, self.stream.cuda_stream)
+        self.size = kx_packed_size(self.ctx)
+        assert self.size == int(self.offsets[-1])
+        kx_build_schwarz(self.ctx, tau_ovlp)
+        kx_build_tree(self.ctx, leaf_max)
+
+    def pack(self, mats):
+        import torch
+        return torch.cat([m.reshape(-1) for m in mats]).contiguous()
+
+    def unpack(self, X):
+        return [X[self.offsets[y]:self.offsets[y + 1]].view(self.n_fn[y], self.n_fn[y]) for y in range(self.n_sys)]
+
+    def __call__(self, P, out=None, **opts):
+        import torch
+        assert P.is_cuda and P.dtype == torch.float64 and P.is_contiguous() and P.numel() == self.size
+        K = out if out is not None else torch.empty_like(P)
+        self.stats = kx_exchange_batch(self.ctx, P.data_ptr(), kx_default_opts(**opts), K.data_ptr())
+        return K
+
+    def host(self, P: np.ndarray, **opts) -> np.ndarray:
+        K = np.zeros_like(P)
+        self.stats = kx_exchange_batch_host(self.ctx, np.ascontiguousarray(P), kx_default_opts(**opts), K)
+        return K
+
+    def worklist(self) -> np.ndarray:
+        return kx_get_worklist(self.ctx)
+
+    def order(self) -> np.ndarray:
+        return kx_get_order(self.ctx, int(self.shell_offsets[-1]))
+
+    def leaves(self):
+        return kx_get_leaves(self.ctx)
+
+    def close(self) -> None:
+        kx_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                kx_destroy(self.ctx)
         except Exception:
             pass

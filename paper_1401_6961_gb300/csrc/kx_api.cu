@@ -47,7 +47,8 @@ void free_all(kx_ctx* c) {
                     c->d_node_nchild, c->d_sq_s, c->d_sq_p, c->d_nrm_s, c->d_nrm_p, c->d_leaf_lo, c->d_leaf_hi,
                     c->d_boys64, c->d_boys32, c->d_pairmap, c->d_scratch, c->d_front[0], c->d_front[1],
                     c->d_mask, c->d_scan, c->d_rec, c->d_bin, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
-                    c->d_hostP, c->d_hostK, c->d_leafdesc, c->d_list};
+                    c->d_hostP, c->d_hostK, c->d_leafdesc, c->d_list, c->d_sseg, c->d_tsys, c->d_lseg,
+                    c->d_node_sys, c->d_mframe};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < NPAIRCLASS; ++i) {
@@ -73,18 +74,27 @@ void kx_default_opts(kx_opts* o) {
     o->chunk_records = 0;
 }
 
-int kx_create(kx_ctx** out, const kx_basis* b, int device, void* cuda_stream) {
+int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int device, void* cuda_stream) {
     if (!out) return KX_EINVAL;
     *out = nullptr;
-    if (!b || !b->xyz || !b->shell_atom || !b->shell_l || !b->shell_alpha) return KX_EINVAL;
-    if (b->n_atom <= 0 || b->n_shell <= 0 || b->n_shell > 65535) return KX_EINVAL;
-    for (int i = 0; i < 3 * b->n_atom; ++i)
-        if (!std::isfinite(b->xyz[i])) return KX_EINVAL;
-    for (int s = 0; s < b->n_shell; ++s) {
-        if (b->shell_atom[s] < 0 || b->shell_atom[s] >= b->n_atom) return KX_EINVAL;
-        if (b->shell_l[s] < 0 || b->shell_l[s] > LMAX) return KX_EINVAL;
-        if (!finite_pos(b->shell_alpha[s])) return KX_EINVAL;
+    if (!bases || n_sys < 1 || n_sys > 65535) return KX_EINVAL;
+    int64_t tot_atom = 0, tot_shell = 0, tot_fn = 0;
+    for (int y = 0; y < n_sys; ++y) {
+        const kx_basis* b = bases + y;
+        if (!b->xyz || !b->shell_atom || !b->shell_l || !b->shell_alpha) return KX_EINVAL;
+        if (b->n_atom <= 0 || b->n_shell <= 0 || b->n_shell > 65535) return KX_EINVAL;
+        for (int i = 0; i < 3 * b->n_atom; ++i)
+            if (!std::isfinite(b->xyz[i])) return KX_EINVAL;
+        for (int s = 0; s < b->n_shell; ++s) {
+            if (b->shell_atom[s] < 0 || b->shell_atom[s] >= b->n_atom) return KX_EINVAL;
+            if (b->shell_l[s] < 0 || b->shell_l[s] > LMAX) return KX_EINVAL;
+            if (!finite_pos(b->shell_alpha[s])) return KX_EINVAL;
+            tot_fn += ncart(b->shell_l[s]);
+        }
+        tot_atom += b->n_atom;
+        tot_shell += b->n_shell;
     }
+    if (tot_shell > (1 << 24) || tot_atom > (1 << 24) || tot_fn > ((int64_t)1 << 30)) return KX_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         (void)cudaGetLastError();
@@ -99,19 +109,52 @@ int kx_create(kx_ctx** out, const kx_basis* b, int device, void* cuda_stream) {
         delete c;
         return KX_ECUDA;
     }
-    c->n_atom = b->n_atom;
-    c->n_shell = b->n_shell;
-    c->xyz.assign(b->xyz, b->xyz + 3 * (size_t)b->n_atom);
-    c->shell_atom.assign(b->shell_atom, b->shell_atom + b->n_shell);
-    c->shell_l.assign(b->shell_l, b->shell_l + b->n_shell);
-    c->shell_alpha.assign(b->shell_alpha, b->shell_alpha + b->n_shell);
-    c->fn_off.resize(b->n_shell + 1);
-    c->fn_off[0] = 0;
-    for (int s = 0; s < b->n_shell; ++s) c->fn_off[s + 1] = c->fn_off[s] + ncart(b->shell_l[s]);
-    c->n_fn = c->fn_off[b->n_shell];
+    // concatenate the systems: atoms, shells and functions system-major
+    c->n_sys = n_sys;
+    c->n_atom = (int)tot_atom;
+    c->n_shell = (int)tot_shell;
+    c->sys_atom.assign(n_sys + 1, 0);
+    c->sys_shell.assign(n_sys + 1, 0);
+    c->sys_fn.assign(n_sys + 1, 0);
+    c->sys_mat.assign(n_sys + 1, 0);
+    c->sseg.resize(n_sys);
+    c->fn_off.assign(1, 0);
+    for (int y = 0; y < n_sys; ++y) {
+        const kx_basis* b = bases + y;
+        const int a0 = c->sys_atom[y];
+        c->xyz.insert(c->xyz.end(), b->xyz, b->xyz + 3 * (size_t)b->n_atom);
+        for (int s = 0; s < b->n_shell; ++s) {
+            c->shell_atom.push_back(a0 + b->shell_atom[s]);
+            c->shell_l.push_back(b->shell_l[s]);
+            c->shell_alpha.push_back(b->shell_alpha[s]);
+            c->fn_off.push_back(c->fn_off.back() + ncart(b->shell_l[s]));
+        }
+        c->sys_atom[y + 1] = a0 + b->n_atom;
+        c->sys_shell[y + 1] = c->sys_shell[y] + b->n_shell;
+        c->sys_fn[y + 1] = c->fn_off.back();
+        const int64_t nf = c->sys_fn[y + 1] - c->sys_fn[y];
+        c->sys_mat[y + 1] = c->sys_mat[y] + nf * nf;
+        c->sseg[y] = Seg{c->sp_total, c->sys_shell[y], b->n_shell};
+        c->sp_total += (int64_t)b->n_shell * b->n_shell;
+    }
+    c->n_fn = c->fn_off.back();
+    for (int s = 0; s < 2 * NCLASS; ++s) {
+        c->eri_threads[s] = ERI_THREADS;
+        c->eri_bpsm[s] = 0;
+    }
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) c->n_sm = 152;
+    std::vector<int32_t> tsys(c->n_shell);
+    for (int y = 0; y < n_sys; ++y)
+        for (int i = c->sys_shell[y]; i < c->sys_shell[y + 1]; ++i) tsys[i] = y;
     int r = KX_OK;
     cudaError_t e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * NCOUNTERS);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * NCOUNTERS, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_sseg, sizeof(Seg) * n_sys);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tsys, sizeof(int32_t) * c->n_shell);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_sseg, c->sseg.data(), sizeof(Seg) * n_sys, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_tsys, tsys.data(), sizeof(int32_t) * c->n_shell, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) r = cuda_check(c, e, "kx_create");
     if (r == KX_OK) r = boys_table(c);
     if (r == KX_OK) r = order_atoms(c);
@@ -122,6 +165,10 @@ int kx_create(kx_ctx** out, const kx_basis* b, int device, void* cuda_stream) {
     }
     *out = c;
     return KX_OK;
+}
+
+int kx_create(kx_ctx** out, const kx_basis* b, int device, void* cuda_stream) {
+    return kx_create_batch(out, 1, b, device, cuda_stream);
 }
 
 int kx_build_schwarz(kx_ctx* c, double tau_ovlp) {
@@ -148,6 +195,12 @@ int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm) {
                 return set_err(c, KX_EINVAL, "perm is not a permutation of the shells");
             seen[perm[i]] = 1;
         }
+        // a batch keeps every system's shells in its own range of tree positions
+        for (int y = 0; y < c->n_sys; ++y) {
+            for (int i = c->sys_shell[y]; i < c->sys_shell[y + 1]; ++i)
+                if (perm[i] < c->sys_shell[y] || perm[i] >= c->sys_shell[y + 1])
+                    return set_err(c, KX_EINVAL, "perm moves a shell out of its system");
+        }
         c->perm.assign(perm, perm + c->n_shell);
         KX_CUDA(c, cudaMemcpyAsync(c->d_perm, c->perm.data(), sizeof(int32_t) * c->n_shell,
                                    cudaMemcpyHostToDevice, c->stream));
@@ -159,11 +212,14 @@ int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm) {
     return build_tree(c, leaf_max_functions);
 }
 
-int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
-                kx_stats* st) {
-    KX_TRY(check_ctx(c));
+}  // extern "C"
+
+namespace {
+
+// ldp = ldk = 0: P and K packed per system (the batch entry points)
+int exchange_impl(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+                  kx_stats* st) {
     if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
-    if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
     if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
     if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
     if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
@@ -195,11 +251,25 @@ int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, doubl
     return r;
 }
 
+}  // namespace
+
+extern "C" {
+
+int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
+                kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
+    if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
+    if (c->n_sys != 1) return set_err(c, KX_EINVAL, "a batch context takes packed P and K (kx_exchange_batch)");
+    return exchange_impl(c, P, ldp, o, K, ldk, st);
+}
+
 int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts* o, double* K_host, int64_t ldk,
                      kx_stats* st) {
     KX_TRY(check_ctx(c));
     if (!P_host || !K_host || !o) return set_err(c, KX_EINVAL, "null argument");
     if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
+    if (c->n_sys != 1) return set_err(c, KX_EINVAL, "a batch context takes packed P and K");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
     size_t n = (size_t)c->n_fn;
@@ -221,7 +291,36 @@ int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts
     return KX_OK;
 }
 
+int kx_exchange_batch(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    return exchange_impl(c, P, 0, o, K, 0, st);
+}
+
+int kx_exchange_batch_host(kx_ctx* c, const double* P_host, const kx_opts* o, double* K_host, kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P_host || !K_host || !o) return set_err(c, KX_EINVAL, "null argument");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    const size_t n = (size_t)c->sys_mat[c->n_sys];
+    if (c->host_cap < n) {
+        cudaFree(c->d_hostP);
+        cudaFree(c->d_hostK);
+        c->d_hostP = c->d_hostK = nullptr;
+        c->host_cap = 0;
+        KX_CUDA(c, cudaMalloc(&c->d_hostP, sizeof(double) * n));
+        KX_CUDA(c, cudaMalloc(&c->d_hostK, sizeof(double) * n));
+        c->host_cap = n;
+    }
+    KX_CUDA(c, cudaMemcpyAsync(c->d_hostP, P_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    KX_TRY(exchange_impl(c, c->d_hostP, 0, o, c->d_hostK, 0, st));
+    KX_CUDA(c, cudaMemcpyAsync(K_host, c->d_hostK, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KX_OK;
+}
+
 int64_t kx_n_functions(const kx_ctx* c) { return c ? c->n_fn : -1; }
+
+int64_t kx_packed_size(const kx_ctx* c) { return c ? c->sys_mat[c->n_sys] : -1; }
 
 int kx_get_order(const kx_ctx* c, int32_t* perm) {
     if (!c || !perm) return KX_EINVAL;
@@ -307,15 +406,20 @@ int kx_get_norms(kx_ctx* c, double* s2, double* pq) {
     if (pq && !c->have_pq) return set_err(c, KX_ESTATE, "no P norms (run kx_exchange)");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
-    const int ns = c->n_shell;
-    std::vector<double> t((size_t)ns * ns);
+    // one dense block per system, in the system's user shell order
+    std::vector<double> t((size_t)c->sp_total);
     const double* src[2] = {c->d_s2, c->d_pq};
     double* dst[2] = {s2, pq};
     for (int k = 0; k < 2; ++k) {
         if (!dst[k]) continue;
         KX_CUDA(c, cudaMemcpy(t.data(), src[k], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
-        for (int i = 0; i < ns; ++i)
-            for (int j = 0; j < ns; ++j) dst[k][(size_t)c->perm[i] * ns + c->perm[j]] = t[(size_t)i * ns + j];
+        for (const Seg& g2 : c->sseg) {
+            const int b = g2.base, n = g2.n;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j)
+                    dst[k][g2.off + (size_t)(c->perm[b + i] - b) * n + (c->perm[b + j] - b)] =
+                        t[g2.off + (size_t)i * n + j];
+        }
     }
     return KX_OK;
 }

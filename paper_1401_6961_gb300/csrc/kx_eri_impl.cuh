@@ -335,7 +335,7 @@ __host__ __device__ constexpr bool use_order_a() {
 // order A: loop nu in c, lam in b
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void contract_a(R* kacc, const R* Rt, const R* eab, const R* ecd,
-                                           const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+                                           const R* __restrict__ Pb, int ldp) {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int LAB = LA + LB, LCD = LC + LD;
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
@@ -345,7 +345,7 @@ __device__ __forceinline__ void contract_a(R* kacc, const R* Rt, const R* eab, c
         sfor<NB>([&](auto ilam_) {
             constexpr int ilam = KX_CV(ilam_);
             constexpr int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
-            const R* prow = P + (int64_t)(fb + ilam) * ldp + fd;
+            const R* prow = Pb + ilam * ldp;
             // T_{h'} = sum_sig E^{cd}_{nu sig,h'} P_{lam sig}
             R Tv[nherm(LCD)];
             sfor<LCD + 1>([&](auto t_) {
@@ -431,7 +431,7 @@ __device__ __forceinline__ void contract_a(R* kacc, const R* Rt, const R* eab, c
 // order B: loop mu in a, sig in d
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void contract_b(R* kacc, const R* Rt, const R* eab, const R* ecd,
-                                           const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+                                           const R* __restrict__ Pb, int ldp) {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int LAB = LA + LB, LCD = LC + LD;
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
@@ -456,7 +456,7 @@ __device__ __forceinline__ void contract_b(R* kacc, const R* Rt, const R* eab, c
             sfor<NB>([&](auto ilam_) {
                 constexpr int ilam = KX_CV(ilam_);
                 constexpr int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
-                const R pv = __ldg(P + (int64_t)(fb + ilam) * ldp + fd + isig);
+                const R pv = __ldg(Pb + ilam * ldp + isig);
                 sfor<mx + lx + 1>([&](auto t_) {
                     constexpr int t = KX_CV(t_);
                     sfor<my + ly + 1>([&](auto u_) {
@@ -527,9 +527,10 @@ __device__ __forceinline__ void contract_b(R* kacc, const R* Rt, const R* eab, c
 // ---------------------------------------------------------------------------
 
 // Sums the per-thread K partials over each run of lanes with the same
-// (fa, fc) and lets the last lane of the run add the sums into K (FP64).
+// (fa, fc) and lets the last lane of the run add the sums into K (FP64) at
+// Kb, the address of K(fa, fc) (row stride ldk).
 template <int NA, int NC, typename R>
-__device__ __forceinline__ void flush_k(R* kacc, int fa, int fc, double* __restrict__ K, int64_t ldk) {
+__device__ __forceinline__ void flush_k(R* kacc, int fa, int fc, double* __restrict__ Kb, int ldk) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long key = fa < 0 ? -1ll : (((long long)fa << 32) | (unsigned)fc);
@@ -546,8 +547,7 @@ __device__ __forceinline__ void flush_k(R* kacc, int fa, int fc, double* __restr
             R o = __shfl_up_sync(full, v, d);
             if (lane - d >= start) v += o;
         }
-        if (tail && key >= 0)
-            atomicAdd(K + (int64_t)(fa + e / NC) * ldk + fc + e % NC, to_f64(v));
+        if (tail && key >= 0) atomicAdd(Kb + (e / NC) * ldk + e % NC, to_f64(v));
     });
 }
 
@@ -555,47 +555,54 @@ __device__ __forceinline__ void flush_k(R* kacc, int fa, int fc, double* __restr
 // the class kernel
 // ---------------------------------------------------------------------------
 
-constexpr int ERI_THREADS = 128;
-
 template <int LA, int LB, int LC, int LD, typename R>
-__global__ void __launch_bounds__(ERI_THREADS)
-k_eri(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra, const PairMeta* __restrict__ bmeta,
-      const R* __restrict__ ket, const PairMeta* __restrict__ kmeta, const R* __restrict__ boys,
-      const R* __restrict__ P, int64_t ldp, double* __restrict__ K, int64_t ldk, int64_t nab, int64_t ncd) {
+__global__ void __launch_bounds__(ERI_MAX_THREADS) k_eri(EriArgs args) {
     constexpr int NA = ncart(LA), NC = ncart(LC);
     constexpr int L = LA + LB + LC + LD;
     constexpr int SAB = rec_stride<R>(LA, LB), SCD = rec_stride<R>(LC, LD);
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
-    const int64_t i = blockIdx.x * (int64_t)ERI_THREADS + threadIdx.x;
-    R kacc[NA * NC];
-    sfor<NA * NC>([&](auto e_) { kacc[KX_CV(e_)] = R(0); });
-    int fa = -1, fc = -1;
-    const Quartet q = i < n ? rec[i] : Quartet{-1, -1};
-    // slots outside the pair tables (never produced by the expansion) are skipped
-    if (q.ab >= 0 && q.ab < nab && q.cd >= 0 && q.cd < ncd) {
-        const R* pb = bra + (int64_t)q.ab * SAB;
-        const R* pk = ket + (int64_t)q.cd * SCD;
-        const PairMeta mb = bmeta[q.ab], mk = kmeta[q.cd];
-        fa = mb.fa;
-        fc = mk.fa;
-        R eab[3 * EAB], ecd[3 * ECD];
-        R p, qq, kab, kcd, X, Y, Z;
-        load_pairs<LA, LB, LC, LD, R>(pb, pk, eab, ecd, p, qq, kab, kcd, X, Y, Z);
-        const R pq = p * qq, sum = p + qq;
-        const R rho = pq / sum;
-        const R r2 = X * X + Y * Y + Z * Z;
-        const R T = rho * r2;
-        const R pref = R(2.0 * 17.493418327624862) * kab * kcd / (pq * Real<R>::sqrt_(sum));
-        R G[L + 1];
-        boys_scaled<L, R>(G, T, rho, r2, pref, boys);
-        R Rt[nherm(L)];
-        hermite_r<L, R>(Rt, G, X, Y, Z);
-        if constexpr (use_order_a<LA, LB, LC, LD>())
-            contract_a<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
-        else
-            contract_b<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
+    const R* __restrict__ bra = (const R*)args.bra;
+    const R* __restrict__ ket = (const R*)args.ket;
+    const R* __restrict__ boys = (const R*)args.boys;
+    const R* __restrict__ P = (const R*)args.P;
+    const int64_t i0 = args.range ? args.range[0] : args.i0, i1 = args.range ? args.range[1] : args.i1;
+    // block-uniform trip count: every warp takes part in every flush
+    for (int64_t base = i0 + blockIdx.x * (int64_t)blockDim.x; base < i1; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        R kacc[NA * NC];
+        sfor<NA * NC>([&](auto e_) { kacc[KX_CV(e_)] = R(0); });
+        int fa = -1, fc = -1, ldk = 0;
+        double* Kb = args.K;
+        const Quartet q = i < i1 ? args.rec[i] : Quartet{-1, -1};
+        // slots outside the pair tables (never produced by the expansion) are skipped
+        if (q.ab >= 0 && q.ab < args.nab && q.cd >= 0 && q.cd < args.ncd) {
+            const R* pb = bra + (int64_t)q.ab * SAB;
+            const R* pk = ket + (int64_t)q.cd * SCD;
+            const PairMeta mb = args.bmeta[q.ab], mk = args.kmeta[q.cd];
+            fa = mb.fa;
+            fc = mk.fa;
+            ldk = mb.ldk;
+            Kb = args.K + mb.krow_a + fc;
+            R eab[3 * EAB], ecd[3 * ECD];
+            R p, qq, kab, kcd, X, Y, Z;
+            load_pairs<LA, LB, LC, LD, R>(pb, pk, eab, ecd, p, qq, kab, kcd, X, Y, Z);
+            const R pq = p * qq, sum = p + qq;
+            const R rho = pq / sum;
+            const R r2 = X * X + Y * Y + Z * Z;
+            const R T = rho * r2;
+            const R pref = R(2.0 * 17.493418327624862) * kab * kcd / (pq * Real<R>::sqrt_(sum));
+            R G[L + 1];
+            boys_scaled<L, R>(G, T, rho, r2, pref, boys);
+            R Rt[nherm(L)];
+            hermite_r<L, R>(Rt, G, X, Y, Z);
+            const R* Pb = P + mb.prow_b + mk.fb;
+            if constexpr (use_order_a<LA, LB, LC, LD>())
+                contract_a<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, Pb, mb.ldp);
+            else
+                contract_b<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, Pb, mb.ldp);
+        }
+        flush_k<NA, NC, R>(kacc, fa, fc, Kb, ldk);
     }
-    flush_k<NA, NC, R>(kacc, fa, fc, K, ldk);
 }
 
 // ---------------------------------------------------------------------------
@@ -641,7 +648,7 @@ __device__ __forceinline__ void hermite_r_rolled(R* Rt, const R* G, R X, R Y, R 
 
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void contract_a_rolled(R* kacc, const R* Rt, const R* eab, const R* ecd,
-                                                  const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+                                                  const R* __restrict__ Pb, int ldp) {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int LAB = LA + LB, LCD = LC + LD;
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
@@ -651,7 +658,7 @@ __device__ __forceinline__ void contract_a_rolled(R* kacc, const R* Rt, const R*
 #pragma unroll 1
         for (int ilam = 0; ilam < NB; ++ilam) {
             const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
-            const R* prow = P + (int64_t)(fb + ilam) * ldp + fd;
+            const R* prow = Pb + ilam * ldp;
             R Tv[nherm(LCD)];
 #pragma unroll 1
             for (int k = 0; k < nherm(LCD); ++k) Tv[k] = R(0);
@@ -713,7 +720,7 @@ __device__ __forceinline__ void contract_a_rolled(R* kacc, const R* Rt, const R*
 
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void contract_b_rolled(R* kacc, const R* Rt, const R* eab, const R* ecd,
-                                                  const R* __restrict__ P, int64_t ldp, int fb, int fd) {
+                                                  const R* __restrict__ Pb, int ldp) {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int LAB = LA + LB, LCD = LC + LD;
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
@@ -729,7 +736,7 @@ __device__ __forceinline__ void contract_b_rolled(R* kacc, const R* Rt, const R*
 #pragma unroll 1
             for (int ilam = 0; ilam < NB; ++ilam) {
                 const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
-                const R pv = __ldg(P + (int64_t)(fb + ilam) * ldp + fd + isig);
+                const R pv = __ldg(Pb + ilam * ldp + isig);
 #pragma unroll 1
                 for (int t = 0; t <= mx + lx; ++t)
 #pragma unroll 1
@@ -783,46 +790,53 @@ __device__ __forceinline__ void contract_b_rolled(R* kacc, const R* Rt, const R*
 }
 
 template <int LA, int LB, int LC, int LD, typename R>
-__global__ void __launch_bounds__(ERI_THREADS)
-k_eri_rolled(const Quartet* __restrict__ rec, int64_t n, const R* __restrict__ bra,
-             const PairMeta* __restrict__ bmeta, const R* __restrict__ ket, const PairMeta* __restrict__ kmeta,
-             const R* __restrict__ boys, const R* __restrict__ P, int64_t ldp, double* __restrict__ K,
-             int64_t ldk, int64_t nab, int64_t ncd) {
+__global__ void __launch_bounds__(ERI_MAX_THREADS) k_eri_rolled(EriArgs args) {
     constexpr int NA = ncart(LA), NC = ncart(LC);
     constexpr int L = LA + LB + LC + LD;
     constexpr int SAB = rec_stride<R>(LA, LB), SCD = rec_stride<R>(LC, LD);
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
-    const int64_t i = blockIdx.x * (int64_t)ERI_THREADS + threadIdx.x;
-    R kacc[NA * NC];
+    const R* __restrict__ bra = (const R*)args.bra;
+    const R* __restrict__ ket = (const R*)args.ket;
+    const R* __restrict__ boys = (const R*)args.boys;
+    const R* __restrict__ P = (const R*)args.P;
+    const int64_t i0 = args.range ? args.range[0] : args.i0, i1 = args.range ? args.range[1] : args.i1;
+    for (int64_t base = i0 + blockIdx.x * (int64_t)blockDim.x; base < i1; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        R kacc[NA * NC];
 #pragma unroll
-    for (int e = 0; e < NA * NC; ++e) kacc[e] = R(0);
-    int fa = -1, fc = -1;
-    const Quartet q = i < n ? rec[i] : Quartet{-1, -1};
-    // slots outside the pair tables (never produced by the expansion) are skipped
-    if (q.ab >= 0 && q.ab < nab && q.cd >= 0 && q.cd < ncd) {
-        const R* pb = bra + (int64_t)q.ab * SAB;
-        const R* pk = ket + (int64_t)q.cd * SCD;
-        const PairMeta mb = bmeta[q.ab], mk = kmeta[q.cd];
-        fa = mb.fa;
-        fc = mk.fa;
-        R eab[3 * EAB], ecd[3 * ECD];
-        R p, qq, kab, kcd, X, Y, Z;
-        load_pairs<LA, LB, LC, LD, R>(pb, pk, eab, ecd, p, qq, kab, kcd, X, Y, Z);
-        const R pq = p * qq, sum = p + qq;
-        const R rho = pq / sum;
-        const R r2 = X * X + Y * Y + Z * Z;
-        const R T = rho * r2;
-        const R pref = R(2.0 * 17.493418327624862) * kab * kcd / (pq * Real<R>::sqrt_(sum));
-        R G[L + 1];
-        boys_scaled<L, R>(G, T, rho, r2, pref, boys);
-        R Rt[nherm(L)];
-        hermite_r_rolled<L, R>(Rt, G, X, Y, Z);
-        if constexpr (use_order_a<LA, LB, LC, LD>())
-            contract_a_rolled<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
-        else
-            contract_b_rolled<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, P, ldp, mb.fb, mk.fb);
+        for (int e = 0; e < NA * NC; ++e) kacc[e] = R(0);
+        int fa = -1, fc = -1, ldk = 0;
+        double* Kb = args.K;
+        const Quartet q = i < i1 ? args.rec[i] : Quartet{-1, -1};
+        // slots outside the pair tables (never produced by the expansion) are skipped
+        if (q.ab >= 0 && q.ab < args.nab && q.cd >= 0 && q.cd < args.ncd) {
+            const R* pb = bra + (int64_t)q.ab * SAB;
+            const R* pk = ket + (int64_t)q.cd * SCD;
+            const PairMeta mb = args.bmeta[q.ab], mk = args.kmeta[q.cd];
+            fa = mb.fa;
+            fc = mk.fa;
+            ldk = mb.ldk;
+            Kb = args.K + mb.krow_a + fc;
+            R eab[3 * EAB], ecd[3 * ECD];
+            R p, qq, kab, kcd, X, Y, Z;
+            load_pairs<LA, LB, LC, LD, R>(pb, pk, eab, ecd, p, qq, kab, kcd, X, Y, Z);
+            const R pq = p * qq, sum = p + qq;
+            const R rho = pq / sum;
+            const R r2 = X * X + Y * Y + Z * Z;
+            const R T = rho * r2;
+            const R pref = R(2.0 * 17.493418327624862) * kab * kcd / (pq * Real<R>::sqrt_(sum));
+            R G[L + 1];
+            boys_scaled<L, R>(G, T, rho, r2, pref, boys);
+            R Rt[nherm(L)];
+            hermite_r_rolled<L, R>(Rt, G, X, Y, Z);
+            const R* Pb = P + mb.prow_b + mk.fb;
+            if constexpr (use_order_a<LA, LB, LC, LD>())
+                contract_a_rolled<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, Pb, mb.ldp);
+            else
+                contract_b_rolled<LA, LB, LC, LD, R>(kacc, Rt, eab, ecd, Pb, mb.ldp);
+        }
+        flush_k<NA, NC, R>(kacc, fa, fc, Kb, ldk);
     }
-    flush_k<NA, NC, R>(kacc, fa, fc, K, ldk);
 }
 
 // ---------------------------------------------------------------------------
@@ -885,45 +899,25 @@ double eri_flops() {
     return f;
 }
 
+// The kernel of a class and precision (unrolled below ROLL_L, rolled above).
 template <int LA, int LB, int LC, int LD>
-int eri_launch_one(kx_ctx* c, int prec, const Quartet* rec, int64_t n, const double* P, int64_t ldp, double* K,
-                   int64_t ldk) {
-    constexpr int pab = LA * 3 + LB, pcd = LC * 3 + LD;
-    if (n <= 0) return KX_OK;
-    unsigned grid = (unsigned)((n + ERI_THREADS - 1) / ERI_THREADS);
-    if constexpr (LA + LB + LC + LD < ROLL_L) {
-        if (prec == 0)
-            k_eri<LA, LB, LC, LD, double><<<grid, ERI_THREADS, 0, c->stream>>>(
-                rec, n, c->d_pair64[pab], c->d_pairmeta[pab], c->d_pair64[pcd], c->d_pairmeta[pcd], c->d_boys64,
-                P, ldp, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
-        else
-            k_eri<LA, LB, LC, LD, float><<<grid, ERI_THREADS, 0, c->stream>>>(
-                rec, n, c->d_pair32[pab], c->d_pairmeta[pab], c->d_pair32[pcd], c->d_pairmeta[pcd], c->d_boys32,
-                c->d_P32, c->n_fn, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
-    } else {
-        if (prec == 0)
-            k_eri_rolled<LA, LB, LC, LD, double><<<grid, ERI_THREADS, 0, c->stream>>>(
-                rec, n, c->d_pair64[pab], c->d_pairmeta[pab], c->d_pair64[pcd], c->d_pairmeta[pcd], c->d_boys64,
-                P, ldp, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
-        else
-            k_eri_rolled<LA, LB, LC, LD, float><<<grid, ERI_THREADS, 0, c->stream>>>(
-                rec, n, c->d_pair32[pab], c->d_pairmeta[pab], c->d_pair32[pcd], c->d_pairmeta[pcd], c->d_boys32,
-                c->d_P32, c->n_fn, K, ldk, c->n_pairs[pab], c->n_pairs[pcd]);
-    }
-    return KX_OK;
+EriKernel eri_kernel(int prec) {
+    if constexpr (LA + LB + LC + LD < ROLL_L)
+        return prec == 0 ? &k_eri<LA, LB, LC, LD, double> : &k_eri<LA, LB, LC, LD, float>;
+    else
+        return prec == 0 ? &k_eri_rolled<LA, LB, LC, LD, double> : &k_eri_rolled<LA, LB, LC, LD, float>;
 }
 
 // dispatch over (lc, ld) for a fixed bra pair class (la, lb)
 #define KX_ERI_CASE(LA_, LB_, LC_, LD_) \
-    case LC_ * 3 + LD_: return eri_launch_one<LA_, LB_, LC_, LD_>(c, prec, rec, n, P, ldp, K, ldk);
+    case LC_ * 3 + LD_: return eri_kernel<LA_, LB_, LC_, LD_>(prec);
 #define KX_ERI_DISPATCH(LA_, LB_)                                                                        \
-    int eri_launch_ab##LA_##LB_(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P, \
-                                int64_t ldp, double* K, int64_t ldk) {                                   \
+    EriKernel eri_kernel_ab##LA_##LB_(int cls, int prec) {                                               \
         switch (cls % 9) {                                                                               \
             KX_ERI_CASE(LA_, LB_, 0, 0) KX_ERI_CASE(LA_, LB_, 0, 1) KX_ERI_CASE(LA_, LB_, 0, 2)          \
             KX_ERI_CASE(LA_, LB_, 1, 0) KX_ERI_CASE(LA_, LB_, 1, 1) KX_ERI_CASE(LA_, LB_, 1, 2)          \
             KX_ERI_CASE(LA_, LB_, 2, 0) KX_ERI_CASE(LA_, LB_, 2, 1) KX_ERI_CASE(LA_, LB_, 2, 2)          \
-            default: return KX_EINVAL;                                                                   \
+            default: return nullptr;                                                                     \
         }                                                                                                \
     }                                                                                                    \
     double class_flops_ab##LA_##LB_(int cls) {                                                           \

@@ -34,7 +34,8 @@ struct ExpandArgs {
     const int32_t* llo;
     const int32_t* lhi;
     const int32_t* tl;
-    int ns;
+    const int32_t* tsys;     // system of every tree position
+    const Seg* sseg;         // shell-pair table block of every system
     const float* slog;
     const float* plog;
     const double* snorm;
@@ -82,8 +83,8 @@ struct WarpTables {
 // the -inf logs of zero Schwarz factors tell.
 template <bool WRITE>
 __device__ __forceinline__ int decide(const ExpandArgs& p, float x, float sab, float scd, int a, int b, int c,
-                                      int d, int cls, int32_t& pab, int32_t& pcd) {
-    const int64_t ab = (int64_t)a * p.ns + b, bd = (int64_t)b * p.ns + d, cd = (int64_t)c * p.ns + d;
+                                      int d, int cls, int64_t t0, int ns, int32_t& pab, int32_t& pcd) {
+    const int64_t ab = t0 + (int64_t)a * ns + b, bd = t0 + (int64_t)b * ns + d, cd = t0 + (int64_t)c * ns + d;
     const bool keep = p.screen ? above(x, p.ltau, p.tau, p.snorm, p.pnorm, ab, bd, cd)
                                : (sab > -INFINITY && scd > -INFINITY);
     if (!keep) return -1;
@@ -146,6 +147,10 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
         const int d0 = p.llo[t.d], nd = p.lhi[t.d] - d0;
         const int total = na * nb * nc * nd;
         ncand += total;
+        // the four leaves belong to one system: its shell-pair block
+        const Seg sg = p.sseg[p.tsys[a0]];
+        const int64_t t0 = sg.t0();
+        const int ns = sg.n;
         const Div md(nd), mb(nb), mc(nc);
         if (na <= STAGE && nb <= STAGE && nc <= STAGE && nd <= STAGE && total < 65536) {
             // stage the leaf quartet's log tables and pair classes
@@ -153,18 +158,18 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
             for (int k = lane; k < na * nb; k += 32) {
                 const int ia = fdiv(k, mb), ib = k - ia * nb;
                 const int a = a0 + ia, b = b0 + ib;
-                tb.sab[ia * STAGE + ib] = __ldg(p.slog + (int64_t)a * p.ns + b);
+                tb.sab[ia * STAGE + ib] = __ldg(p.slog + t0 + (int64_t)a * ns + b);
                 tb.cab[ia * STAGE + ib] = (uint8_t)(__ldg(p.tl + a) * 3 + __ldg(p.tl + b));
             }
             for (int k = lane; k < nc * nd; k += 32) {
                 const int ic = fdiv(k, md), id = k - ic * nd;
                 const int c = c0 + ic, d = d0 + id;
-                tb.scd[ic * STAGE + id] = __ldg(p.slog + (int64_t)c * p.ns + d);
+                tb.scd[ic * STAGE + id] = __ldg(p.slog + t0 + (int64_t)c * ns + d);
                 tb.ccd[ic * STAGE + id] = (uint8_t)(__ldg(p.tl + c) * 3 + __ldg(p.tl + d));
             }
             for (int k = lane; k < nb * nd; k += 32) {
                 const int ib = fdiv(k, md), id = k - ib * nd;
-                tb.pbd[ib * STAGE + id] = __ldg(p.plog + (int64_t)(b0 + ib) * p.ns + d0 + id);
+                tb.pbd[ib * STAGE + id] = __ldg(p.plog + t0 + (int64_t)(b0 + ib) * ns + d0 + id);
             }
             __syncwarp();
             // column maxima for the (b,d) pre-filter
@@ -218,7 +223,8 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const float sab = tb.sab[ia * STAGE + ib], scd = tb.scd[ic * STAGE + id];
                     const float x = sab + tb.pbd[ib * STAGE + id] + scd;
                     const int cls = tb.cab[ia * STAGE + ib] * 9 + tb.ccd[ic * STAGE + id];
-                    stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, pab, pcd);
+                    stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns, pab,
+                                           pcd);
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
             }
@@ -235,10 +241,10 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const int ic = r % nc;
                     const int ia = r / nc;
                     const int a = a0 + ia, b = b0 + ib, c = c0 + ic, d = d0 + id;
-                    const float sab = p.slog[(int64_t)a * p.ns + b], scd = p.slog[(int64_t)c * p.ns + d];
-                    const float x = sab + p.plog[(int64_t)b * p.ns + d] + scd;
+                    const float sab = p.slog[t0 + (int64_t)a * ns + b], scd = p.slog[t0 + (int64_t)c * ns + d];
+                    const float x = sab + p.plog[t0 + (int64_t)b * ns + d] + scd;
                     const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
-                    stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, pab, pcd);
+                    stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, t0, ns, pab, pcd);
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
             }
@@ -261,7 +267,8 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
     a.llo = c->d_leaf_lo;
     a.lhi = c->d_leaf_hi;
     a.tl = c->d_tl;
-    a.ns = c->n_shell;
+    a.tsys = c->d_tsys;
+    a.sseg = c->d_sseg;
     a.slog = c->d_slog;
     a.plog = c->d_plog;
     a.snorm = c->d_snorm;
@@ -306,20 +313,59 @@ int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
 // class dispatch
 // ---------------------------------------------------------------------------
 
-int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P, int64_t ldp,
-               double* K, int64_t ldk) {
+EriKernel eri_kernel(int cls, int prec) {
     switch (cls / 9) {
-        case 0: return eri_launch_ab00(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 1: return eri_launch_ab01(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 2: return eri_launch_ab02(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 3: return eri_launch_ab10(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 4: return eri_launch_ab11(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 5: return eri_launch_ab12(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 6: return eri_launch_ab20(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 7: return eri_launch_ab21(c, cls, prec, rec, n, P, ldp, K, ldk);
-        case 8: return eri_launch_ab22(c, cls, prec, rec, n, P, ldp, K, ldk);
-        default: return set_err(c, KX_EINVAL, "bad class");
+        case 0: return eri_kernel_ab00(cls, prec);
+        case 1: return eri_kernel_ab01(cls, prec);
+        case 2: return eri_kernel_ab02(cls, prec);
+        case 3: return eri_kernel_ab10(cls, prec);
+        case 4: return eri_kernel_ab11(cls, prec);
+        case 5: return eri_kernel_ab12(cls, prec);
+        case 6: return eri_kernel_ab20(cls, prec);
+        case 7: return eri_kernel_ab21(cls, prec);
+        case 8: return eri_kernel_ab22(cls, prec);
+        default: return nullptr;
     }
+}
+
+EriArgs eri_args(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1, const int64_t* range,
+                 const double* P, double* K) {
+    const int pab = cls / 9, pcd = cls % 9;
+    EriArgs a;
+    a.rec = rec;
+    a.i0 = i0;
+    a.i1 = i1;
+    a.range = range;
+    a.bmeta = c->d_pairmeta[pab];
+    a.kmeta = c->d_pairmeta[pcd];
+    a.bra = prec == 0 ? (const void*)c->d_pair64[pab] : (const void*)c->d_pair32[pab];
+    a.ket = prec == 0 ? (const void*)c->d_pair64[pcd] : (const void*)c->d_pair32[pcd];
+    a.boys = prec == 0 ? (const void*)c->d_boys64 : (const void*)c->d_boys32;
+    a.P = prec == 0 ? (const void*)P : (const void*)c->d_P32;
+    a.K = K;
+    a.nab = c->n_pairs[pab];
+    a.ncd = c->n_pairs[pcd];
+    return a;
+}
+
+int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1, const int64_t* range,
+               const double* P, double* K) {
+    if (!range && i1 <= i0) return KX_OK;
+    EriKernel k = eri_kernel(cls, prec);
+    if (!k) return set_err(c, KX_EINVAL, "bad class");
+    const int s = prec * NCLASS + cls;
+    const int threads = c->eri_threads[s];
+    int64_t blocks;
+    if (range) {
+        // device-side range (captured launches): always a persistent grid
+        blocks = (int64_t)std::max(c->eri_bpsm[s], 4) * c->n_sm;
+    } else {
+        blocks = (i1 - i0 + threads - 1) / threads;
+        if (c->eri_bpsm[s] > 0) blocks = std::min<int64_t>(blocks, (int64_t)c->eri_bpsm[s] * c->n_sm);
+    }
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)1 << 30));
+    k<<<(unsigned)blocks, threads, 0, c->stream>>>(eri_args(c, cls, prec, rec, i0, i1, range, P, K));
+    return KX_OK;
 }
 
 double class_flops(int cls) {

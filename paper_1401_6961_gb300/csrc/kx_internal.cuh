@@ -72,11 +72,49 @@ enum { P32_P = 0, P32_INV2P = 1, P32_KAB = 2, P32_PHI = 3, P32_PLO = 6, P32_PA =
 // row length of the FP32 Boys table (orders 0..BOYS_M, padded for 16-byte loads)
 constexpr int BOYS32_ROW = 16;
 
-// Shell pair metadata shared by the FP64 and FP32 pair tables.
+// Shell pair metadata shared by the FP64 and FP32 pair tables.  P and K
+// entries of one system are addressed affinely in user function indices:
+// X(mu,nu) = X[x0 + mu * ld + nu] (see MatFrame); a pair (a,b) carries the
+// row bases it needs as a bra.
 struct PairMeta {
+    int64_t prow_b;   // P offset of row fb, column 0 (p0 + fb * ldp)
+    int64_t krow_a;   // K offset of row fa, column 0 (k0 + fa * ldk)
     int32_t fa, fb;   // user function offsets of the two shells
-    int32_t a, b;     // tree positions
+    int32_t ldp, ldk; // leading dimensions of the pair's system
 };
+
+// One square diagonal block of a block-diagonal table: entries (i,j) with
+// base <= i, j < base + n sit at off + (i - base) * n + (j - base), i.e. at
+// t0() + i * n + j.  A single system is one block with base 0.
+struct Seg {
+    int64_t off;
+    int32_t base, n;
+    __host__ __device__ int64_t t0() const { return off - (int64_t)base * (n + 1); }
+};
+
+// P and K addressing of one system for one build: X(mu,nu) at
+// x0 + mu * ld + nu (mu, nu user function indices of the system).
+struct MatFrame {
+    int64_t p0, k0;
+    int32_t ldp, ldk;
+};
+
+// block of a flat table index (binary search over the blocks' offsets)
+__host__ __device__ inline int seg_find(const Seg* __restrict__ seg, int nseg, int64_t e) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (seg[m].off <= e) lo = m; else hi = m - 1;
+    }
+    return lo;
+}
+// (i, j) of flat index e of a block-diagonal table
+__host__ __device__ inline void seg_pair(const Seg* __restrict__ seg, int nseg, int64_t e, int& i, int& j) {
+    const Seg s = seg[seg_find(seg, nseg, e)];
+    const int64_t r = e - s.off;
+    i = s.base + (int)(r / s.n);
+    j = s.base + (int)(r % s.n);
+}
 
 // Shell quartet record: slots in the bra (la,lb) and ket (lc,ld) pair tables.
 struct Quartet {
@@ -110,6 +148,22 @@ struct kx_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err = "no error";
+
+    // systems: a context holds n_sys independent systems, each contiguous
+    // in atoms, shells (user order and tree positions) and functions; every
+    // table is block-diagonal over them (one block for a single system)
+    int n_sys = 1;
+    std::vector<int32_t> sys_atom, sys_shell;   // [n_sys + 1] offsets
+    std::vector<int64_t> sys_fn, sys_mat;       // [n_sys + 1]; sys_mat: packed P/K (sum of n_fn^2)
+    std::vector<kx::Seg> sseg;                  // shell-pair blocks, [n_sys]
+    int64_t sp_total = 0;                       // entries of a shell-pair table
+    kx::Seg* d_sseg = nullptr;
+    int32_t* d_tsys = nullptr;                  // system of every tree position
+    std::vector<kx::Seg> lseg;                  // level blocks, [(depth + 1) * n_sys], off absolute
+    kx::Seg* d_lseg = nullptr;
+    int32_t* d_node_sys = nullptr;              // system of every node (flat over levels)
+    kx::MatFrame* d_mframe = nullptr;           // [n_sys], per build
+    bool packed = false;                        // the current build's P/K are packed per system
 
     // basis (host copies)
     int n_atom = 0, n_shell = 0;
@@ -206,6 +260,11 @@ struct kx_ctx {
     size_t list_cap = 0;
     bool have_pq = false;
     int64_t launches = 0;                 // kernels launched by the current build
+    // launch shape of every (precision, class) stream: threads per block and
+    // persistent blocks per SM (0 = one thread per record); see kx_autotune
+    int eri_threads[2 * kx::NCLASS] = {};
+    int eri_bpsm[2 * kx::NCLASS] = {};
+    int n_sm = 0;
     // per-stream profile of the last profiled build
     double prof_ms[2 * kx::NCLASS] = {};
     int64_t prof_n[2 * kx::NCLASS] = {};
@@ -252,7 +311,9 @@ int order_atoms(kx_ctx* c);                                  // kx_setup.cu
 int schwarz(kx_ctx* c, double tau_ovlp);                      // kx_setup.cu
 int build_tree(kx_ctx* c, int leaf_max);                      // kx_setup.cu
 int boys_table(kx_ctx* c);                                    // kx_setup.cu
-int p_norms(kx_ctx* c, const double* P, int64_t ldp);         // kx_setup.cu
+// P/K addressing of the current build: ldp = ldk = 0 means packed per system
+int set_frames(kx_ctx* c, int64_t ldp, int64_t ldk, bool packed);   // kx_setup.cu
+int p_norms(kx_ctx* c, const double* P);                      // kx_setup.cu
 int pair_tables(kx_ctx* c, double tau, bool want32);          // kx_setup.cu
 int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);  // kx_traverse.cu
 int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
@@ -276,37 +337,58 @@ int expand_count(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, do
                  int mixed, int shell_screen, int64_t* bin);
 int expand_write(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
                  int mixed, int shell_screen, int64_t* bin_off, Quartet* rec);
-// launches the class kernel (la,lb,lc,ld) for n records; prec 0 = FP64, 1 = FP32
-// (prec 1 reads the FP32 copy of P, c->d_P32, leading dimension n_fn)
-int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-               int64_t ldp, double* K, int64_t ldk);
-int eri_launch_ab00(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
+// ERI class kernels (kx_eri_impl.cuh).  Launch shapes: any multiple of 32
+// threads up to ERI_MAX_THREADS; the grid strides over the records, so a
+// persistent grid (a few blocks per SM) and one thread per record run the
+// same code.
+constexpr int ERI_THREADS = 128;       // default block size
+constexpr int ERI_MAX_THREADS = 256;
+
+// The records of one (class, precision) stream: rec[i] for i in [i0, i1),
+// or, with range != nullptr, in [range[0], range[1]) read on the device.
+// P is the FP64 P or its FP32 copy (same layout); both are addressed
+// through the pair tables' row bases.
+struct EriArgs {
+    const Quartet* rec;
+    int64_t i0, i1;
+    const int64_t* range;
+    const PairMeta* bmeta;
+    const PairMeta* kmeta;
+    const void* bra;
+    const void* ket;
+    const void* boys;
+    const void* P;
+    double* K;
+    int64_t nab, ncd;
+};
+typedef void (*EriKernel)(EriArgs);
+
+EriKernel eri_kernel(int cls, int prec);          // kx_expand.cu, over the nine below
+EriKernel eri_kernel_ab00(int cls, int prec);
+EriKernel eri_kernel_ab01(int cls, int prec);
+EriKernel eri_kernel_ab02(int cls, int prec);
+EriKernel eri_kernel_ab10(int cls, int prec);
+EriKernel eri_kernel_ab11(int cls, int prec);
+EriKernel eri_kernel_ab12(int cls, int prec);
+EriKernel eri_kernel_ab20(int cls, int prec);
+EriKernel eri_kernel_ab21(int cls, int prec);
+EriKernel eri_kernel_ab22(int cls, int prec);
 double class_flops_ab00(int cls);
-int eri_launch_ab01(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab01(int cls);
-int eri_launch_ab02(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab02(int cls);
-int eri_launch_ab10(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab10(int cls);
-int eri_launch_ab11(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab11(int cls);
-int eri_launch_ab12(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab12(int cls);
-int eri_launch_ab20(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab20(int cls);
-int eri_launch_ab21(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab21(int cls);
-int eri_launch_ab22(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t n, const double* P,
-                    int64_t ldp, double* K, int64_t ldk);
 double class_flops_ab22(int cls);
+// arguments of stream (cls, prec) over rec[i0, i1) (or the device range)
+EriArgs eri_args(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1,
+                 const int64_t* range, const double* P, double* K);
+// launches the class kernel of stream (cls, prec) with the context's launch
+// shape for that stream
+int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1, const int64_t* range,
+               const double* P, double* K);
 
 // algorithmic FLOPs of one shell quartet of a class (the counter of the ERI kernels)
 double class_flops(int cls);

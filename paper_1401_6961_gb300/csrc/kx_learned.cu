@@ -419,6 +419,7 @@ struct Guard {
 extern "C" {
 
 int kx_traverse(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, int64_t* n_leaves) {
+    if (c && c->n_sys != 1) return set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (!c) return KX_EINVAL;
     if (!P || !o || !n_leaves) return set_err(c, KX_EINVAL, "null argument");
     if (ldp < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
@@ -436,6 +437,7 @@ int kx_traverse(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, int64
 
 int kx_evaluate_kept(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
                      kx_stats* st) {
+    if (c && c->n_sys != 1) return set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (!c) return KX_EINVAL;
     if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
     if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
@@ -453,6 +455,7 @@ int kx_evaluate_kept(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, 
 
 int kx_exchange_leaves(kx_ctx* c, const double* P, int64_t ldp, const int32_t* leaves, int64_t n, const kx_opts* o,
                        double* K, int64_t ldk, kx_stats* st) {
+    if (c && c->n_sys != 1) return set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (!c) return KX_EINVAL;
     if (!P || !K || !o || (n > 0 && !leaves) || n < 0) return set_err(c, KX_EINVAL, "bad argument");
     if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
@@ -481,6 +484,7 @@ int kx_exchange_leaves(kx_ctx* c, const double* P, int64_t ldp, const int32_t* l
 }
 
 int kx_leaf_features(kx_ctx* c, float* feat, int64_t cap, int64_t* n) {
+    if (c && c->n_sys != 1) return set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (!c) return KX_EINVAL;
     if (!n || cap < 0 || (cap > 0 && !feat)) return set_err(c, KX_EINVAL, "bad argument");
     if (!c->keep_valid || !c->have_pq) return set_err(c, KX_ESTATE, "no kept leaf list (kx_traverse first)");
@@ -502,6 +506,7 @@ int kx_leaf_features(kx_ctx* c, float* feat, int64_t cap, int64_t* n) {
 }
 
 int kx_cull_kept(kx_ctx* c, const float* pred, double tau, double log10_budget, int64_t* n_kept) {
+    if (c && c->n_sys != 1) return set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (!c) return KX_EINVAL;
     if (!n_kept || (!pred && c->keep_n > 0) || !std::isfinite(tau) || tau < 0.0 || std::isnan(log10_budget))
         return set_err(c, KX_EINVAL, "bad argument");
@@ -537,6 +542,7 @@ int kx_cull_kept(kx_ctx* c, const float* pred, double tau, double log10_budget, 
 }
 
 int kx_block_norms(kx_ctx* c, const double* K, int64_t ldk, const int32_t* leaves, int64_t n, double* norms) {
+    if (c && c->n_sys != 1) return set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (!c) return KX_EINVAL;
     if (!K || ldk < c->n_fn || n < 0 || (n > 0 && (!leaves || !norms))) return set_err(c, KX_EINVAL, "bad argument");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");

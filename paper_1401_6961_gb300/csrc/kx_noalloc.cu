@@ -186,6 +186,7 @@ struct Guard {
 extern "C" int kx_traverse_level_noalloc(kx_ctx* c, int32_t level, const uint16_t* front, int64_t n, double tau,
                                          uint16_t* next, int64_t cap, int64_t* n_next) {
     if (!c) return KX_EINVAL;
+    if (c->n_sys != 1) return kx::set_err(c, KX_ENOTIMPL, "single-system contexts only");
     if (n > NA_MAX)
         return kx::set_err(c, KX_ECAPACITY, "frontier of " + std::to_string(n) + " tasks exceeds the " +
                                                 std::to_string(NA_MAX) + "-task limit of the no-allocation path");

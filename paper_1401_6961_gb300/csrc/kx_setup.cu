@@ -65,10 +65,15 @@ __device__ uint64_t hilbert_key3(uint32_t x0, uint32_t x1, uint32_t x2, int bits
     return key;
 }
 
-// One block: bounding box, keys, ranks of the atoms.
-__global__ void k_atom_keys(const double* __restrict__ xyz, int n, uint64_t* __restrict__ key,
-                           int32_t* __restrict__ rank) {
+// One block per system: bounding box, keys, ranks of the system's atoms
+// (atoms [ao[s], ao[s+1]); ranks count from ao[s]).
+__global__ void k_atom_keys(const double* __restrict__ xyz, const int32_t* __restrict__ ao,
+                            uint64_t* __restrict__ key, int32_t* __restrict__ rank) {
     __shared__ double s_lo[3], s_hi[3];
+    const int a0 = ao[blockIdx.x], n = ao[blockIdx.x + 1] - a0;
+    xyz += 3 * (int64_t)a0;
+    key += a0;
+    rank += a0;
     if (threadIdx.x < 3) {
         double lo = xyz[threadIdx.x], hi = xyz[threadIdx.x];
         for (int a = 1; a < n; ++a) {
@@ -105,18 +110,25 @@ __global__ void k_atom_keys(const double* __restrict__ xyz, int n, uint64_t* __r
             uint64_t kb = key[b];
             r += (kb < ka) || (kb == ka && b < a);
         }
-        rank[a] = r;
+        rank[a] = a0 + r;
     }
 }
 
-// Tree position of every shell: atoms by rank, input order inside an atom.
+// Tree position of every shell: atoms by rank, input order inside an atom,
+// within the shell range [so[y], so[y+1]) of the shell's system y.
 __global__ void k_shell_pos(const int32_t* __restrict__ shell_atom, const int32_t* __restrict__ rank,
-                            int ns, int32_t* __restrict__ perm) {
+                            const int32_t* __restrict__ so, int nsys, int ns, int32_t* __restrict__ perm) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ns) return;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (so[m] <= s) lo = m; else hi = m - 1;
+    }
+    const int t0 = so[lo], t1 = so[lo + 1];
     int ra = rank[shell_atom[s]];
-    int pos = 0;
-    for (int t = 0; t < ns; ++t) {
+    int pos = t0;
+    for (int t = t0; t < t1; ++t) {
         int rt = rank[shell_atom[t]];
         pos += (rt < ra) || (rt == ra && t < s);
     }
@@ -124,23 +136,27 @@ __global__ void k_shell_pos(const int32_t* __restrict__ shell_atom, const int32_
 }
 
 int order_atoms(kx_ctx* c) {
-    int n = c->n_atom, ns = c->n_shell;
+    int n = c->n_atom, ns = c->n_shell, nsys = c->n_sys;
     double* d_xyz = nullptr;
     uint64_t* d_key = nullptr;
-    int32_t *d_rank = nullptr, *d_sa = nullptr;
+    int32_t *d_rank = nullptr, *d_sa = nullptr, *d_ao = nullptr, *d_so = nullptr;
     auto cleanup = [&]() {
-        cudaFree(d_xyz); cudaFree(d_key); cudaFree(d_rank); cudaFree(d_sa);
+        cudaFree(d_xyz); cudaFree(d_key); cudaFree(d_rank); cudaFree(d_sa); cudaFree(d_ao); cudaFree(d_so);
     };
     cudaError_t e = cudaMalloc(&d_xyz, sizeof(double) * 3 * n);
     if (e == cudaSuccess) e = cudaMalloc(&d_key, sizeof(uint64_t) * n);
     if (e == cudaSuccess) e = cudaMalloc(&d_rank, sizeof(int32_t) * n);
     if (e == cudaSuccess) e = cudaMalloc(&d_sa, sizeof(int32_t) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ao, sizeof(int32_t) * (nsys + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_so, sizeof(int32_t) * (nsys + 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_perm, sizeof(int32_t) * ns);
     if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "order_atoms alloc"); }
     cudaMemcpyAsync(d_xyz, c->xyz.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(d_sa, c->shell_atom.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream);
-    k_atom_keys<<<1, 1024, 0, c->stream>>>(d_xyz, n, d_key, d_rank);
-    k_shell_pos<<<(ns + 255) / 256, 256, 0, c->stream>>>(d_sa, d_rank, ns, c->d_perm);
+    cudaMemcpyAsync(d_ao, c->sys_atom.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_so, c->sys_shell.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream);
+    k_atom_keys<<<nsys, 1024, 0, c->stream>>>(d_xyz, d_ao, d_key, d_rank);
+    k_shell_pos<<<(ns + 255) / 256, 256, 0, c->stream>>>(d_sa, d_rank, d_so, nsys, ns, c->d_perm);
     c->perm.resize(ns);
     cudaMemcpyAsync(c->perm.data(), c->d_perm, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, c->stream);
     e = cudaStreamSynchronize(c->stream);
@@ -232,13 +248,13 @@ __device__ double norm_prim(double a, int l) {
 
 // One thread per unordered pair a <= b (tree positions).  (ab|ab) has
 // P = Q, so T = 0, F_n(0) = 1/(2n+1), and R depends on rho = p/2 only.
-__global__ void k_schwarz(int ns, const int32_t* __restrict__ tl, const double* __restrict__ tctr,
-                          const double* __restrict__ talpha, double tau_ovlp,
+__global__ void k_schwarz(const Seg* __restrict__ seg, int nseg, int64_t npair, const int32_t* __restrict__ tl,
+                          const double* __restrict__ tctr, const double* __restrict__ talpha, double tau_ovlp,
                           double* __restrict__ s2, double* __restrict__ snorm, float* __restrict__ slog) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t npair = (int64_t)ns * ns;
     if (idx >= npair) return;
-    int a = (int)(idx / ns), b = (int)(idx % ns);
+    const Seg sg = seg[seg_find(seg, nseg, idx)];
+    const int a = sg.base + (int)((idx - sg.off) / sg.n), b = sg.base + (int)((idx - sg.off) % sg.n);
     if (a > b) return;
     int la = tl[a], lb = tl[b];
     double A[3] = {tctr[3 * a], tctr[3 * a + 1], tctr[3 * a + 2]};
@@ -320,7 +336,7 @@ __global__ void k_schwarz(int ns, const int32_t* __restrict__ tl, const double* 
     }
     double nrm = sqrt(total);
     float lg = total > 0.0 ? (float)log2(nrm) : -INFINITY;
-    int64_t i1 = (int64_t)a * ns + b, i2 = (int64_t)b * ns + a;
+    int64_t i1 = idx, i2 = sg.t0() + (int64_t)b * sg.n + a;
     s2[i1] = total; s2[i2] = total;
     snorm[i1] = nrm; snorm[i2] = nrm;
     slog[i1] = lg; slog[i2] = lg;
@@ -343,7 +359,7 @@ __global__ void k_tree_basis(int ns, const int32_t* __restrict__ perm, const int
 
 int schwarz(kx_ctx* c, double tau_ovlp) {
     int ns = c->n_shell;
-    int64_t n2 = (int64_t)ns * ns;
+    int64_t n2 = c->sp_total;
     // upload the basis in user order, gather it into tree order
     std::vector<double> ctr(3 * (size_t)ns);
     std::vector<int32_t> foff(ns);
@@ -378,8 +394,9 @@ int schwarz(kx_ctx* c, double tau_ovlp) {
     cudaMemcpyAsync(d_alpha, c->shell_alpha.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->stream);
     k_tree_basis<<<(ns + 255) / 256, 256, 0, c->stream>>>(ns, c->d_perm, d_l, d_ctr, d_alpha, d_foff, c->d_tl,
                                                           c->d_tctr, c->d_talpha, c->d_tfoff);
-    k_schwarz<<<(unsigned)((n2 + 127) / 128), 128, 0, c->stream>>>(ns, c->d_tl, c->d_tctr, c->d_talpha, tau_ovlp,
-                                                                 c->d_s2, c->d_snorm, c->d_slog);
+    k_schwarz<<<(unsigned)((n2 + 127) / 128), 128, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, c->d_tl, c->d_tctr,
+                                                                 c->d_talpha, tau_ovlp, c->d_s2, c->d_snorm,
+                                                                 c->d_slog);
     e = cudaStreamSynchronize(c->stream);
     cudaFree(d_l); cudaFree(d_foff); cudaFree(d_ctr); cudaFree(d_alpha);
     if (e != cudaSuccess) return cuda_check(c, e, "schwarz");
@@ -427,21 +444,25 @@ __device__ int block_excl_scan(int v, int* sh, int* total) {
 // split at the shell boundary s in (lo, hi) minimising
 // |2 pre[s] - pre[lo] - pre[hi]|, the lower s on a tie.
 __global__ void __launch_bounds__(TREE_THREADS)
-k_build_tree(int ns, const int32_t* __restrict__ tl, int leaf_max, int max_nodes, int32_t* __restrict__ pre,
-             int32_t* __restrict__ lo, int32_t* __restrict__ hi, int32_t* __restrict__ child,
-             int32_t* __restrict__ nchild, int32_t* __restrict__ level_n, int32_t* __restrict__ status) {
+k_build_tree(int ns, const int32_t* __restrict__ tl, const int32_t* __restrict__ roots, int nroot, int leaf_max,
+             int max_nodes, int32_t* __restrict__ pre, int32_t* __restrict__ lo, int32_t* __restrict__ hi,
+             int32_t* __restrict__ child, int32_t* __restrict__ nchild, int32_t* __restrict__ level_n,
+             int32_t* __restrict__ status) {
     __shared__ int sh[32];
     __shared__ int s_n, s_off, s_done;
-    // function-count prefix sums (sequential: ns <= 65535, once per geometry)
+    // function-count prefix sums (sequential, once per geometry); level 0
+    // holds one root per system, [roots[i], roots[i+1])
     if (threadIdx.x == 0) {
         pre[0] = 0;
         for (int s = 0; s < ns; ++s) pre[s + 1] = pre[s] + ncart(tl[s]);
-        lo[0] = 0;
-        hi[0] = ns;
-        s_n = 1;
+        s_n = nroot;
         s_off = 0;
         s_done = 0;
         status[0] = 0;
+    }
+    for (int i = threadIdx.x; i < nroot; i += blockDim.x) {
+        lo[i] = roots[i];
+        hi[i] = roots[i + 1];
     }
     __syncthreads();
     int level = 0;
@@ -510,47 +531,57 @@ k_build_tree(int ns, const int32_t* __restrict__ tl, int leaf_max, int max_nodes
 // norm pyramids (Eq. 2): squared Frobenius norms per level, bottom-up
 // ---------------------------------------------------------------------------
 
-// deepest level: sum over the shells of the two leaves, a outer, b inner
-__global__ void k_pyr_leaves(int nl, int ns, const int32_t* __restrict__ llo, const int32_t* __restrict__ lhi,
+// Deepest level: sum over the shells of the two leaves, a outer, b inner.
+// Flat index e over the level's block-diagonal table (blocks lseg, one per
+// system, offsets absolute); the shell table block of the same system.
+__global__ void k_pyr_leaves(int64_t e0, int64_t e1, const Seg* __restrict__ lseg, const Seg* __restrict__ sseg,
+                             int nsys, const int32_t* __restrict__ llo, const int32_t* __restrict__ lhi,
                              const double* __restrict__ sq_shell, double* __restrict__ sq,
                              double* __restrict__ nrm) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= (int64_t)nl * nl) return;
-    int X = (int)(i / nl), Y = (int)(i % nl);
+    int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= e1) return;
+    const int y = seg_find(lseg, nsys, i);
+    const Seg lg = lseg[y], sg = sseg[y];
+    const int X = lg.base + (int)((i - lg.off) / lg.n), Y = lg.base + (int)((i - lg.off) % lg.n);
+    const int64_t t0 = sg.t0();
     double s = 0.0;
     for (int a = llo[X]; a < lhi[X]; ++a)
-        for (int b = llo[Y]; b < lhi[Y]; ++b) s = __dadd_rn(s, sq_shell[(int64_t)a * ns + b]);
+        for (int b = llo[Y]; b < lhi[Y]; ++b) s = __dadd_rn(s, sq_shell[t0 + (int64_t)a * sg.n + b]);
     sq[i] = s;
     nrm[i] = sqrt(s);
 }
 
 // level k from level k+1: children pairs in order (0,0),(0,1),(1,0),(1,1)
-__global__ void k_pyr_up(int n, int nn, const int32_t* __restrict__ child, const int32_t* __restrict__ nchild,
-                         const double* __restrict__ sq_next, double* __restrict__ sq, double* __restrict__ nrm) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * n) return;
-    int X = (int)(i / n), Y = (int)(i % n);
+__global__ void k_pyr_up(int64_t e0, int64_t e1, const Seg* __restrict__ lseg, const Seg* __restrict__ lseg_next,
+                         int nsys, const int32_t* __restrict__ child, const int32_t* __restrict__ nchild,
+                         const double* sq_all, double* sq, double* __restrict__ nrm) {
+    int64_t i = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= e1) return;
+    const int y = seg_find(lseg, nsys, i);
+    const Seg lg = lseg[y], ng = lseg_next[y];
+    const int X = lg.base + (int)((i - lg.off) / lg.n), Y = lg.base + (int)((i - lg.off) % lg.n);
+    const int64_t t0 = ng.t0();
     int cx = child[X], cy = child[Y], nx = nchild[X], ny = nchild[Y];
     double s = 0.0;
     for (int ii = 0; ii < nx; ++ii)
-        for (int jj = 0; jj < ny; ++jj) s = __dadd_rn(s, sq_next[(int64_t)(cx + ii) * nn + (cy + jj)]);
+        for (int jj = 0; jj < ny; ++jj) s = __dadd_rn(s, sq_all[t0 + (int64_t)(cx + ii) * ng.n + (cy + jj)]);
     sq[i] = s;
     nrm[i] = sqrt(s);
 }
 
 static int build_pyramid(kx_ctx* c, const double* sq_shell, double* sq, double* nrm) {
-    int D = c->depth;
-    int nl = c->levels[D].n;
-    int64_t n2 = (int64_t)nl * nl;
-    k_pyr_leaves<<<(unsigned)((n2 + 255) / 256), 256, 0, c->stream>>>(nl, c->n_shell, c->d_leaf_lo, c->d_leaf_hi,
-                                                                    sq_shell, sq + c->pyr_off[D], nrm + c->pyr_off[D]);
+    const int D = c->depth, ny = c->n_sys;
+    {
+        const int64_t e0 = c->pyr_off[D], e1 = c->pyr_off[D + 1];
+        k_pyr_leaves<<<(unsigned)((e1 - e0 + 255) / 256), 256, 0, c->stream>>>(
+            e0, e1, c->d_lseg + (size_t)D * ny, c->d_sseg, ny, c->d_leaf_lo, c->d_leaf_hi, sq_shell, sq, nrm);
+    }
     c->launches += 1 + D;
     for (int k = D - 1; k >= 0; --k) {
-        int n = c->levels[k].n, nn = c->levels[k + 1].n;
-        int64_t m = (int64_t)n * n;
-        k_pyr_up<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(
-            n, nn, c->d_node_child + c->levels[k].off, c->d_node_nchild + c->levels[k].off,
-            sq + c->pyr_off[k + 1], sq + c->pyr_off[k], nrm + c->pyr_off[k]);
+        const int64_t e0 = c->pyr_off[k], e1 = c->pyr_off[k + 1];
+        k_pyr_up<<<(unsigned)((e1 - e0 + 255) / 256), 256, 0, c->stream>>>(
+            e0, e1, c->d_lseg + (size_t)k * ny, c->d_lseg + (size_t)(k + 1) * ny, ny,
+            c->d_node_child + c->levels[k].off, c->d_node_nchild + c->levels[k].off, sq, sq, nrm);
     }
     return KX_OK;
 }
@@ -569,13 +600,20 @@ int build_tree(kx_ctx* c, int leaf_max) {
         cudaFree(d_leveln); cudaFree(d_status);
     };
     if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "build_tree alloc"); }
-    k_build_tree<<<1, TREE_THREADS, 0, c->stream>>>(ns, c->d_tl, leaf_max, max_nodes, d_pre, d_lo, d_hi, d_child,
-                                                    d_nchild, d_leveln, d_status);
+    int32_t* d_roots = nullptr;
+    e = cudaMalloc(&d_roots, sizeof(int32_t) * (c->n_sys + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_roots, c->sys_shell.data(), sizeof(int32_t) * (c->n_sys + 1), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e != cudaSuccess) { cudaFree(d_roots); cleanup(); return cuda_check(c, e, "build_tree alloc"); }
+    k_build_tree<<<1, TREE_THREADS, 0, c->stream>>>(ns, c->d_tl, d_roots, c->n_sys, leaf_max, max_nodes, d_pre, d_lo,
+                                                    d_hi, d_child, d_nchild, d_leveln, d_status);
     int32_t status[2] = {0, 0};
     std::vector<int32_t> leveln(MAX_LEVELS, 0);
     cudaMemcpyAsync(status, d_status, sizeof(status), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(leveln.data(), d_leveln, sizeof(int32_t) * MAX_LEVELS, cudaMemcpyDeviceToHost, c->stream);
     e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_roots);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "build_tree"); }
     if (status[0] != 0) {
@@ -617,9 +655,40 @@ int build_tree(kx_ctx* c, int leaf_max) {
                     c->stream);
     cudaMemcpyAsync(c->d_leaf_hi, c->node_hi.data() + c->levels[D].off, sizeof(int32_t) * nl, cudaMemcpyHostToDevice,
                     c->stream);
-    // pyramid storage
+    // per-level blocks: the nodes of a level are system-major (level 0 holds
+    // the roots in system order and children follow their parents)
+    const int ny = c->n_sys;
+    std::vector<int32_t> node_sys(total);
+    c->lseg.assign((size_t)(D + 1) * ny, Seg{0, 0, 0});
     c->pyr_off.assign(D + 2, 0);
-    for (int k = 0; k <= D; ++k) c->pyr_off[k + 1] = c->pyr_off[k] + (int64_t)c->levels[k].n * c->levels[k].n;
+    for (int k = 0; k <= D; ++k) {
+        if (c->levels[k].n > 65535) return set_err(c, KX_ECAPACITY, "more than 65535 nodes in one tree level");
+        int y = 0;
+        for (int X = 0; X < c->levels[k].n; ++X) {
+            const int lo = c->node_lo[c->levels[k].off + X];
+            while (y + 1 < ny && c->sys_shell[y + 1] <= lo) ++y;
+            node_sys[c->levels[k].off + X] = y;
+            Seg& g = c->lseg[(size_t)k * ny + y];
+            if (g.n == 0) g.base = X;
+            g.n++;
+        }
+        int64_t off = c->pyr_off[k];
+        for (int y2 = 0; y2 < ny; ++y2) {
+            Seg& g = c->lseg[(size_t)k * ny + y2];
+            if (g.n == 0) return set_err(c, KX_ECUDA, "tree level without a node of some system");
+            g.off = off;
+            off += (int64_t)g.n * g.n;
+        }
+        c->pyr_off[k + 1] = off;
+    }
+    cudaFree(c->d_lseg); cudaFree(c->d_node_sys);
+    c->d_lseg = nullptr; c->d_node_sys = nullptr;
+    e = cudaMalloc(&c->d_lseg, sizeof(Seg) * c->lseg.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_node_sys, sizeof(int32_t) * total);
+    if (e != cudaSuccess) return cuda_check(c, e, "build_tree alloc");
+    cudaMemcpyAsync(c->d_lseg, c->lseg.data(), sizeof(Seg) * c->lseg.size(), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_node_sys, node_sys.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, c->stream);
+    // pyramid storage
     int64_t pyr = c->pyr_off[D + 1];
     cudaFree(c->d_sq_s); cudaFree(c->d_sq_p); cudaFree(c->d_nrm_s); cudaFree(c->d_nrm_p);
     c->d_sq_s = c->d_sq_p = c->d_nrm_s = c->d_nrm_p = nullptr;
@@ -639,17 +708,21 @@ int build_tree(kx_ctx* c, int leaf_max) {
 // P shell-block norms and their pyramid
 // ===========================================================================
 
-__global__ void k_p_shell(int ns, const int32_t* __restrict__ tl, const int32_t* __restrict__ tfoff,
-                          const double* __restrict__ P, int64_t ldp, double* __restrict__ pq,
-                          double* __restrict__ pn, float* __restrict__ plog) {
+__global__ void k_p_shell(const Seg* __restrict__ seg, int nseg, int64_t n2, const int32_t* __restrict__ tl,
+                          const int32_t* __restrict__ tfoff, const MatFrame* __restrict__ mf,
+                          const double* __restrict__ P, double* __restrict__ pq, double* __restrict__ pn,
+                          float* __restrict__ plog) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= (int64_t)ns * ns) return;
-    int b = (int)(i / ns), d = (int)(i % ns);
+    if (i >= n2) return;
+    const int y = seg_find(seg, nseg, i);
+    const Seg sg = seg[y];
+    const int b = sg.base + (int)((i - sg.off) / sg.n), d = sg.base + (int)((i - sg.off) % sg.n);
+    const MatFrame f = mf[y];
     int fb = tfoff[b], fd = tfoff[d], nb = ncart(tl[b]), nd = ncart(tl[d]);
     double s = 0.0;
     for (int x = 0; x < nb; ++x)
-        for (int y = 0; y < nd; ++y) {
-            double v = P[(int64_t)(fb + x) * ldp + fd + y];
+        for (int z = 0; z < nd; ++z) {
+            double v = P[f.p0 + (int64_t)(fb + x) * f.ldp + fd + z];
             s = __dadd_rn(s, __dmul_rn(v, v));
         }
     pq[i] = s;
@@ -658,9 +731,30 @@ __global__ void k_p_shell(int ns, const int32_t* __restrict__ tl, const int32_t*
     plog[i] = s > 0.0 ? (float)log2(r) : -INFINITY;
 }
 
-int p_norms(kx_ctx* c, const double* P, int64_t ldp) {
-    int ns = c->n_shell;
-    int64_t n2 = (int64_t)ns * ns;
+int set_frames(kx_ctx* c, int64_t ldp, int64_t ldk, bool packed) {
+    const int ny = c->n_sys;
+    std::vector<MatFrame> f(ny);
+    for (int y = 0; y < ny; ++y) {
+        if (packed) {
+            const int64_t n = c->sys_fn[y + 1] - c->sys_fn[y], f0 = c->sys_fn[y];
+            // X(mu,nu) = X[mat_y + (mu - f0) * n + (nu - f0)]
+            f[y].p0 = f[y].k0 = c->sys_mat[y] - f0 * (n + 1);
+            f[y].ldp = f[y].ldk = (int32_t)n;
+        } else {
+            f[y].p0 = f[y].k0 = 0;
+            f[y].ldp = (int32_t)ldp;
+            f[y].ldk = (int32_t)ldk;
+        }
+    }
+    if (!c->d_mframe) KX_CUDA(c, cudaMalloc(&c->d_mframe, sizeof(MatFrame) * ny));
+    KX_CUDA(c, cudaMemcpyAsync(c->d_mframe, f.data(), sizeof(MatFrame) * ny, cudaMemcpyHostToDevice, c->stream));
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->packed = packed;
+    return KX_OK;
+}
+
+int p_norms(kx_ctx* c, const double* P) {
+    int64_t n2 = c->sp_total;
     cudaError_t e = cudaSuccess;
     if (!c->d_pq) {
         e = cudaMalloc(&c->d_pq, sizeof(double) * n2);
@@ -668,8 +762,8 @@ int p_norms(kx_ctx* c, const double* P, int64_t ldp) {
         if (e == cudaSuccess) e = cudaMalloc(&c->d_plog, sizeof(float) * n2);
         if (e != cudaSuccess) return cuda_check(c, e, "p_norms alloc");
     }
-    k_p_shell<<<(unsigned)((n2 + 255) / 256), 256, 0, c->stream>>>(ns, c->d_tl, c->d_tfoff, P, ldp, c->d_pq,
-                                                                  c->d_pnorm, c->d_plog);
+    k_p_shell<<<(unsigned)((n2 + 255) / 256), 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, c->d_tl, c->d_tfoff,
+                                                                  c->d_mframe, P, c->d_pq, c->d_pnorm, c->d_plog);
     c->launches++;
     KX_TRY(build_pyramid(c, c->d_pq, c->d_sq_p, c->d_nrm_p));
     c->have_pq = true;
@@ -727,25 +821,29 @@ int boys_table(kx_ctx* c) {
 // that the different rounding order of the quartet bound can never keep a
 // quartet whose pair was dropped.  Pairs emptied by Eq. 4 (s2 = 0) never
 // take part.
-__global__ void k_pair_flags(int ns, const int32_t* __restrict__ tl, const double* __restrict__ snorm,
-                             const double* __restrict__ s2, double tau, double pmax, double smax, int screen,
-                             int cls, int64_t* __restrict__ flag) {
+__global__ void k_pair_flags(const Seg* __restrict__ seg, int nseg, int64_t n2, const int32_t* __restrict__ tl,
+                             const double* __restrict__ snorm, const double* __restrict__ s2, double tau,
+                             double pmax, double smax, int screen, int cls, int64_t* __restrict__ flag) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= (int64_t)ns * ns) return;
-    int a = (int)(i / ns), b = (int)(i % ns);
+    if (i >= n2) return;
+    int a, b;
+    seg_pair(seg, nseg, i, a, b);
     int ok = (tl[a] * 3 + tl[b] == cls) && s2[i] > 0.0;
     if (ok && screen) ok = __dmul_rn(__dmul_rn(snorm[i], pmax), smax) > tau * (1.0 - 0x1p-40);
     flag[i] = ok;
 }
 
-__global__ void k_pair_fill(int ns, int cls, const int32_t* __restrict__ tl, const double* __restrict__ tctr,
+__global__ void k_pair_fill(const Seg* __restrict__ seg, int nseg, int64_t n2, int cls,
+                            const int32_t* __restrict__ tl, const double* __restrict__ tctr,
                             const double* __restrict__ talpha, const int32_t* __restrict__ tfoff,
-                            const int64_t* __restrict__ flag, const int64_t* __restrict__ slot,
-                            int32_t* __restrict__ pairmap, PairMeta* __restrict__ meta,
-                            double* __restrict__ d64, float* __restrict__ d32) {
+                            const MatFrame* __restrict__ mf, const int64_t* __restrict__ flag,
+                            const int64_t* __restrict__ slot, int32_t* __restrict__ pairmap,
+                            PairMeta* __restrict__ meta, double* __restrict__ d64, float* __restrict__ d32) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= (int64_t)ns * ns) return;
-    int a = (int)(i / ns), b = (int)(i % ns);
+    if (i >= n2) return;
+    const int y = seg_find(seg, nseg, i);
+    const Seg sg = seg[y];
+    const int a = sg.base + (int)((i - sg.off) / sg.n), b = sg.base + (int)((i - sg.off) % sg.n);
     if (tl[a] * 3 + tl[b] != cls) return;
     if (!flag[i]) {
         pairmap[i] = -1;
@@ -754,7 +852,9 @@ __global__ void k_pair_fill(int ns, int cls, const int32_t* __restrict__ tl, con
     int64_t s = slot[i];
     pairmap[i] = (int32_t)s;
     int la = tl[a], lb = tl[b];
-    meta[s] = PairMeta{tfoff[a], tfoff[b], a, b};
+    const MatFrame f = mf[y];
+    meta[s] = PairMeta{f.p0 + (int64_t)tfoff[b] * f.ldp, f.k0 + (int64_t)tfoff[a] * f.ldk, tfoff[a], tfoff[b],
+                       f.ldp, f.ldk};
     double al = talpha[a], be = talpha[b], p = al + be;
     double A[3] = {tctr[3 * a], tctr[3 * a + 1], tctr[3 * a + 2]};
     double B[3] = {tctr[3 * b], tctr[3 * b + 1], tctr[3 * b + 2]};
@@ -794,8 +894,7 @@ __global__ void k_max_reduce(const double* __restrict__ x, int64_t n, unsigned l
 }
 
 int pair_tables(kx_ctx* c, double tau, bool screen) {
-    int ns = c->n_shell;
-    int64_t n2 = (int64_t)ns * ns;
+    int64_t n2 = c->sp_total;
     // maxima of S and of the P shell-block norms
     unsigned long long* d_mx = c->d_counters;   // two slots
     cudaMemsetAsync(d_mx, 0, 2 * sizeof(unsigned long long), c->stream);
@@ -815,8 +914,8 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
     unsigned g = (unsigned)((n2 + 255) / 256);
     for (int cls = 0; cls < NPAIRCLASS; ++cls) {
         int la = cls / 3, lb = cls % 3;
-        k_pair_flags<<<g, 256, 0, c->stream>>>(ns, c->d_tl, c->d_snorm, c->d_s2, tau, pmax, smax, screen ? 1 : 0,
-                                               cls, flag);
+        k_pair_flags<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, c->d_tl, c->d_snorm, c->d_s2, tau, pmax,
+                                               smax, screen ? 1 : 0, cls, flag);
         int64_t total = 0;
         KX_TRY(exclusive_scan(c, flag, slot, n2, &total));
         c->n_pairs[cls] = total;
@@ -835,8 +934,9 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
             }
             c->pair_cap[cls] = (int64_t)cap;
         }
-        k_pair_fill<<<g, 256, 0, c->stream>>>(ns, cls, c->d_tl, c->d_tctr, c->d_talpha, c->d_tfoff, flag, slot,
-                                              c->d_pairmap, c->d_pairmeta[cls], c->d_pair64[cls], c->d_pair32[cls]);
+        k_pair_fill<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, cls, c->d_tl, c->d_tctr, c->d_talpha,
+                                              c->d_tfoff, c->d_mframe, flag, slot, c->d_pairmap, c->d_pairmeta[cls],
+                                              c->d_pair64[cls], c->d_pair32[cls]);
         c->launches += 2;
     }
     return KX_OK;

@@ -133,13 +133,19 @@ int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_
 // traversal kernels
 // ===========================================================================
 
-// bound of every child of every task at the next level; survivors as a mask
+// bound of every child of every task at the next level; survivors as a mask.
+// The next level's norms of the task's system sit at t0 + X * n + Y
+// (block lseg_next[system]).
 __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const int32_t* __restrict__ child,
-                              const int32_t* __restrict__ nchild, const double* __restrict__ S,
-                              const double* __restrict__ Pn, int nn, double tau, uint16_t* __restrict__ mask,
+                              const int32_t* __restrict__ nchild, const int32_t* __restrict__ node_sys,
+                              const Seg* __restrict__ lseg_next, const double* __restrict__ S,
+                              const double* __restrict__ Pn, double tau, uint16_t* __restrict__ mask,
                               int64_t* __restrict__ cnt) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const Task t = front[i];
+        const Seg g = lseg_next[node_sys[t.a]];
+        const int64_t t0 = g.t0();
+        const int nn = g.n;
         const int ca = child[t.a], na = nchild[t.a];
         const int cb = child[t.b], nb = nchild[t.b];
         const int cc = child[t.c], nc = nchild[t.c];
@@ -147,11 +153,11 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
         unsigned m = 0;
         for (int ia = 0; ia < na; ++ia)
             for (int ib = 0; ib < nb; ++ib) {
-                const double sab = S[(int64_t)(ca + ia) * nn + (cb + ib)];
+                const double sab = S[t0 + (int64_t)(ca + ia) * nn + (cb + ib)];
                 for (int id = 0; id < nd; ++id) {
-                    const double x = __dmul_rn(sab, Pn[(int64_t)(cb + ib) * nn + (cd + id)]);
+                    const double x = __dmul_rn(sab, Pn[t0 + (int64_t)(cb + ib) * nn + (cd + id)]);
                     for (int ic = 0; ic < nc; ++ic) {
-                        const double beta = __dmul_rn(x, S[(int64_t)(cc + ic) * nn + (cd + id)]);
+                        const double beta = __dmul_rn(x, S[t0 + (int64_t)(cc + ic) * nn + (cd + id)]);
                         if (beta > tau) m |= 1u << (((ia * 2 + ib) * 2 + ic) * 2 + id);
                     }
                 }
@@ -180,12 +186,18 @@ __global__ void k_expand_write(const Task* __restrict__ front, int64_t p0, int64
     }
 }
 
-// a tree that is a single leaf: the one task, kept iff its bound exceeds tau
-__global__ void k_root_only(const double* __restrict__ S, const double* __restrict__ Pn, double tau,
-                            Task* __restrict__ out, int64_t* __restrict__ n_out) {
-    double beta = __dmul_rn(__dmul_rn(S[0], Pn[0]), S[0]);
-    n_out[0] = beta > tau ? 1 : 0;
-    out[0] = Task{0, 0, 0, 0};
+// trees that are single leaves: the root task of every system, kept iff its
+// bound exceeds tau, in system order (one thread: only for tiny systems)
+__global__ void k_root_only(const Seg* __restrict__ lseg0, int nsys, const double* __restrict__ S,
+                            const double* __restrict__ Pn, double tau, Task* __restrict__ out,
+                            int64_t* __restrict__ n_out) {
+    int64_t k = 0;
+    for (int y = 0; y < nsys; ++y) {
+        const int64_t i = lseg0[y].off;   // the block of a one-node level: (y, y)
+        const double beta = __dmul_rn(__dmul_rn(S[i], Pn[i]), S[i]);
+        if (beta > tau) out[k++] = Task{(uint16_t)y, (uint16_t)y, (uint16_t)y, (uint16_t)y};
+    }
+    n_out[0] = k;
 }
 
 // chunk boundaries: b_j = first parent whose output offset is >= j * cap
@@ -203,9 +215,15 @@ __global__ void k_chunk_bounds(const int64_t* __restrict__ off, int64_t n, int64
     bounds[j] = a;
 }
 
-__global__ void k_to_f32(const double* __restrict__ P, int64_t ldp, int64_t n, float* __restrict__ P32) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x)
-        P32[i] = __double2float_rn(P[(i / n) * ldp + (i % n)]);
+// FP32 copy of P in the same layout: n rows of n entries at stride ldp
+// (a packed batch is one row of all its entries)
+__global__ void k_to_f32(const double* __restrict__ P, int64_t ldp, int64_t rows, int64_t n,
+                         float* __restrict__ P32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (i / n) * ldp + (i % n);
+        P32[j] = __double2float_rn(P[j]);
+    }
 }
 
 // ===========================================================================
@@ -300,7 +318,7 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
             cudaEventCreate(&e1);
             cudaEventRecord(e0, c->stream);
         }
-        KX_TRY(eri_launch(c, cls, prec, c->d_rec + off[s], (int64_t)h[s], r.P, r.ldp, r.K, r.ldk));
+        KX_TRY(eri_launch(c, cls, prec, c->d_rec, off[s], off[s + 1], nullptr, r.P, r.K));
         if (r.o->profile) {
             cudaEventRecord(e1, c->stream);
             c->prof_ev.push_back({s, {e0, e1}});
@@ -366,13 +384,22 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
         cudaEventDestroy(pe.second.second);
     }
     c->prof_ev.clear();
+    // ldp = ldk = 0: P and K are packed per system
+    const bool packed = ldp == 0 && ldk == 0;
+    KX_TRY(set_frames(c, ldp, ldk, packed));
     tm.mark(ST_NORMS);
-    if (evaluate)
-        KX_CUDA(c, cudaMemset2DAsync(K, sizeof(double) * ldk, 0, sizeof(double) * c->n_fn, c->n_fn, c->stream));
-    KX_TRY(p_norms(c, P, ldp));
+    const int64_t mat_total = c->sys_mat[c->n_sys];
+    if (evaluate) {
+        if (packed)
+            KX_CUDA(c, cudaMemsetAsync(K, 0, sizeof(double) * mat_total, c->stream));
+        else
+            KX_CUDA(c, cudaMemset2DAsync(K, sizeof(double) * ldk, 0, sizeof(double) * c->n_fn, c->n_fn, c->stream));
+    }
+    KX_TRY(p_norms(c, P));
     if (evaluate && o->precision == KX_MIXED) {
-        KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)c->n_fn * c->n_fn));
-        k_to_f32<<<1024, 256, 0, c->stream>>>(P, ldp, c->n_fn, c->d_P32);
+        const int64_t rows = packed ? 1 : c->n_fn, cols = packed ? mat_total : c->n_fn, ld = packed ? 0 : ldp;
+        KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)((rows - 1) * ld + cols)));
+        k_to_f32<<<1024, 256, 0, c->stream>>>(P, ld, rows, cols, c->d_P32);
         c->launches++;
     }
     if (evaluate) KX_TRY(pair_tables(c, o->tau, o->shell_screen != 0));
@@ -392,17 +419,23 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     tm.mark(ST_TRAV);
     const double* S = c->d_nrm_s;
     const double* Pn = c->d_nrm_p;
-    KX_TRY(grow(c, &c->d_front[0], &c->front_cap[0], 16));
-    Task root{0, 0, 0, 0};
-    KX_CUDA(c, cudaMemcpyAsync(c->d_front[0], &root, sizeof(Task), cudaMemcpyHostToDevice, c->stream));
-    int64_t nfront = 1;
+    // level 0: the root task (Y, Y, Y, Y) of every system Y
+    const int ny = c->n_sys;
+    KX_TRY(grow(c, &c->d_front[0], &c->front_cap[0], (size_t)ny + 16));
+    {
+        std::vector<Task> roots(ny);
+        for (int y = 0; y < ny; ++y) roots[y] = Task{(uint16_t)y, (uint16_t)y, (uint16_t)y, (uint16_t)y};
+        KX_CUDA(c, cudaMemcpyAsync(c->d_front[0], roots.data(), sizeof(Task) * ny, cudaMemcpyHostToDevice,
+                                   c->stream));
+        KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    int64_t nfront = ny;
     int cur = 0;
-    st->n_tasks[0] = 1;
+    st->n_tasks[0] = ny;
     if (D == 0) {
-        int64_t* d_n = c->d_scan;
         KX_TRY(grow(c, &c->d_scan, &c->scan_cap, 16));
-        d_n = c->d_scan;
-        k_root_only<<<1, 1, 0, c->stream>>>(S, Pn, o->tau, c->d_front[0], d_n);
+        int64_t* d_n = c->d_scan;
+        k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], d_n);
         c->launches++;
         int64_t nk = 0;
         KX_CUDA(c, cudaMemcpyAsync(&nk, d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
@@ -413,18 +446,17 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
         if (evaluate) KX_TRY(process_leaves(r, c->d_front[0], nk));
     } else {
         for (int k = 0; k < D; ++k) {
-            const int nn = c->levels[k + 1].n;
             const int32_t* child = c->d_node_child + c->levels[k].off;
             const int32_t* nchild = c->d_node_nchild + c->levels[k].off;
-            const double* Sk = S + c->pyr_off[k + 1];
-            const double* Pk = Pn + c->pyr_off[k + 1];
+            const int32_t* nsys = c->d_node_sys + c->levels[k].off;
+            const Seg* lnext = c->d_lseg + (size_t)(k + 1) * ny;
             KX_TRY(grow(c, &c->d_mask, &c->mask_cap, (size_t)nfront));
             KX_TRY(grow(c, &c->d_scan, &c->scan_cap, (size_t)2 * nfront));
             int64_t* cnt = c->d_scan;
             int64_t* off = c->d_scan + nfront;
             unsigned g = (unsigned)std::min<int64_t>((nfront + 255) / 256, 152 * 64);
-            k_expand_mask<<<g, 256, 0, c->stream>>>(c->d_front[cur], nfront, child, nchild, Sk, Pk, nn, o->tau,
-                                                    c->d_mask, cnt);
+            k_expand_mask<<<g, 256, 0, c->stream>>>(c->d_front[cur], nfront, child, nchild, nsys, lnext, S, Pn,
+                                                    o->tau, c->d_mask, cnt);
             c->launches++;
             int64_t total = 0;
             KX_TRY(exclusive_scan(c, cnt, off, nfront, &total));

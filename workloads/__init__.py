@@ -251,6 +251,15 @@ def water_batch(count: int = 256, seed_base: int = 3, lo: int = 4, hi: int = 48)
     return [water_cluster(int(n), seed_base * 100000 + i, "small") for i, n in enumerate(sizes)]
 
 
+def batch_workload(count: int = 256, seed_base: int = 3, lo: int = 4, hi: int = 48
+                   ) -> Tuple[List[System], List[np.ndarray]]:
+    """The batched workload: ``water_batch`` clusters, each with its own
+    density (cluster i of seed base s: seed s * 100000 + i + 1000)."""
+    systems = water_batch(count, seed_base, lo, hi)
+    dens = [density(x, seed_base * 100000 + i + 1000) for i, x in enumerate(systems)]
+    return systems, dens
+
+
 def _place_nerf(a: np.ndarray, b: np.ndarray, c: np.ndarray, bond: float,
                 angle_deg: float, torsion_deg: float) -> np.ndarray:
     """Atom d bonded to c with angle b-c-d and torsion a-b-c-d."""
