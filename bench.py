@@ -31,7 +31,8 @@ if ROOT not in sys.path:
 
 METRIC = "K-builds/s & ERI quartets/s vs plain FP64 GPU path at max|ΔK|≤1e-8"
 UNIT = "K-builds/s"
-WORKLOADS = ("water64", "water16")
+WORKLOADS = ("water64", "water16", "batch256")
+BATCH_TAU = 1e-8
 TAU = 1e-10
 SPLIT = 1e-4
 L2_FLUSH_BYTES = 256 << 20
@@ -132,11 +133,53 @@ def oracle_sample(sys_, P, n_rows: int, seed: int = 1):
     return dt, 1.0 / full, oracle.num_threads(), desc
 
 
+def oracle_batch_sample(systems, dens, n_sys: int, n_rows: int, seed: int = 1):
+    """Exact screened K rows of n_rows shells in each of n_sys sampled
+    systems of a batch, extrapolated to every shell of every system."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(len(systems), size=n_sys, replace=False)
+    t_all = 0.0
+    est = 0.0
+    for y in picks:
+        s = systems[int(y)]
+        rows = [int(x) for x in rng.choice(s.n_shell, size=n_rows, replace=False)]
+        t0 = time.perf_counter()
+        oracle.exchange_screened(s, dens[int(y)], BATCH_TAU, rows=rows)
+        dt = time.perf_counter() - t0
+        t_all += dt
+        est += dt * s.n_shell / n_rows
+    full = est * len(systems) / n_sys
+    desc = (f"oracle (FP64 C, OpenMP) screened exchange of {n_rows} sampled K-row shells in each of {n_sys} "
+            f"sampled clusters ({t_all:.1f} s), extrapolated to every shell of the {len(systems)} clusters")
+    return t_all, len(systems) / full, oracle.num_threads(), desc
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import workloads as wl
+    if args.workload == "batch256":
+        systems, dens = wl.batch_workload()
+        rates = []
+        threads, desc = 1, ""
+        for i in range(args.warmup + args.steps):
+            dt, rate, threads, desc = oracle_batch_sample(systems, dens, 32, 4 * args.ref_rows, seed=100 + i)
+            if i >= args.warmup:
+                rates.append(rate)
+        v = statistics.mean(rates)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": batch_config(systems, "fp64"),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     sys_, P = wl.workload(args.workload)
     # warm-up steps and timed steps, each a bounded sample of the workload
     times = []
@@ -170,9 +213,166 @@ def workload_config(sys_, precision, name):
             "parallelism": "replicas"}
 
 
+def batch_config(systems, precision):
+    nw = [s.n_atom // 3 for s in systems]
+    return {"workload": f"{len(systems)} independent water clusters of 4-48 molecules (drawn {min(nw)}-{max(nw)}), "
+                        f"1 g/cm^3, small even-tempered basis (13 functions per water; "
+                        f"{sum(s.n_fn for s in systems)} functions in all), each with its own density, "
+                        f"tau={BATCH_TAU:g}",
+            "name": "batch256", "systems": len(systems), "tau": BATCH_TAU, "leaf_max": 10,
+            "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
+            "shell_screen": True, "launch": "one captured CUDA graph per batch build (autotuned class-kernel shapes)",
+            "l2": "inputs larger than L2 (packed P and K 297 MB each), and a 256 MB buffer written between steps",
+            "parallelism": "replicas"}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def run_batch(args):
+    """The batched workload: 256 clusters per step, replayed from one CUDA graph."""
+    import numpy as np
+    import torch
+
+    import paper_1401_6961_gb300 as kx
+    import workloads as wl
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kx.load()
+    systems, dens = wl.batch_workload()
+    stream = torch.cuda.current_stream(dev)
+    bx = kx.BatchExchange(systems, device=local, stream=stream)
+    Pd = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).to(dev)
+    Kd = torch.empty_like(Pd)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    mixed = dict(tau=BATCH_TAU, precision=kx.KX_MIXED, split_threshold=SPLIT)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # set-up (untimed): launch-shape autotuning, then the captured plan
+    bx.autotune(Pd, out=Kd, **mixed)
+    n_tuned = bx.n_tuned
+    bx.plan(Pd, Kd, headroom=0.25, **mixed)
+    for _ in range(args.warmup):
+        bx.replay()
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    evs = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bx.replay()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(dev)
+    barrier()
+    st = bx.stats
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+    ms_step = ms / args.steps
+    nsys = len(systems)
+    value = ws * nsys * 1e3 / ms_step
+    Kmix = Kd.clone()
+
+    # per-class profile of an eager mixed build with the same launch shapes
+    bx(Pd, out=Kd, profile=1, **mixed)
+    prof = kx.kx_get_profile(bx.ctx)
+    ste = bx.stats
+    s_dom = int(np.argmax(prof["ms"]))
+    prec_dom = "fp64" if s_dom < 81 else "fp32"
+    cls = s_dom % 81
+    la, lb, lc, ld = cls // 27, (cls // 9) % 3, (cls // 3) % 3, cls % 3
+    peak64 = kx.kx_peak_probe(local, kx.KX_FP64) / 1e3
+    peak32 = kx.kx_peak_probe(local, kx.KX_MIXED) / 1e3
+    peak = peak64 if prec_dom == "fp64" else peak32
+    achieved = prof["flops"][s_dom] / (prof["ms"][s_dom] * 1e-3) / 1e12
+
+    fp64 = None
+    diff = None
+    if args.fp64_steps > 0:
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            bx(Pd, out=Kd, tau=BATCH_TAU, precision=kx.KX_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = max_over_ranks(e0.elapsed_time(e1)) / args.fp64_steps
+        diff = float((Kmix - Kd).abs().max().item())
+        fp64 = {"value": ws * nsys * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+                "warmup": 0, "launch": "eager", "quartets_per_s": ws * bx.stats.n_shell_quartets / (ms64 * 1e-3)}
+
+    e2e = None
+    if args.e2e_steps > 0:
+        Ph = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).pin_memory().numpy()
+        Kh = torch.empty(Ph.shape[0], dtype=torch.float64).pin_memory().numpy()
+        o = kx.kx_default_opts(**mixed)
+        kx.kx_exchange_batch_host(bx.ctx, Ph, o, Kh)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            kx.kx_exchange_batch_host(bx.ctx, Ph, o, Kh)
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": ws * nsys * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * Ph.shape[0],
+               "d2h_bytes_per_step": 8 * Ph.shape[0], "launch": "eager (kx_exchange_batch_host)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        dt, rate, thr, desc = oracle_batch_sample(systems, dens, 32, 4 * args.ref_rows)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": batch_config(systems, "mixed"),
+            "quartets_per_s": ws * st.n_shell_quartets / (ms_step * 1e-3),
+            "shell_quartets": st.n_shell_quartets, "leaf_quartets": st.n_leaf_quartets,
+            "shell_quartets_fp64": st.n_shell_quartets_fp64,
+            "stages_ms_eager": {"norms": ste.ms_norms, "traverse": ste.ms_traverse, "expand": ste.ms_expand,
+                                "eri": ste.ms_eri, "total": ste.ms_total},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"k_eri<{la},{lb},{lc},{ld},{'double' if prec_dom == 'fp64' else 'float'}>",
+                         "measured": "CUDA events around each launch of that kernel in an eager profiled build "
+                                     "of the same batch (a graph replay cannot be split by events)",
+                         "peak_source": f"measured FMA probe ({prec_dom} pipe), kx_peak_probe"},
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
+            "max_abs_dK_vs_fp64": diff,
+            "streams_tuned": n_tuned,
+            "e2e": e2e,
+            "gpu_launches": int(st.n_launches) * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    bx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
 
 def run_ours(args):
     import numpy as np
@@ -346,7 +546,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=WORKLOADS, default="water64",
-                    help="water64 is the benchmark; water16 is a small case for profiling")
+                    help="water64 is the benchmark; water16 is a small case for profiling; batch256 is the "
+                         "batched workload (256 clusters per step, captured graph)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-rows", type=int, default=2, help="K-row shells per oracle sample")
@@ -354,6 +555,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batch(args)
     else:
         run_ours(args)
 

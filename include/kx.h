@@ -171,6 +171,37 @@ int kx_exchange_batch_host(kx_ctx* c, const double* P_host, const kx_opts* o, do
 /* Doubles of a packed P or K: sum over the systems of n_y^2. */
 int64_t kx_packed_size(const kx_ctx* c);
 
+/* Launch-shape autotuner of the class kernels: one kx_exchange_batch build
+ * (P, K packed, K written) during which every (precision, class) stream with
+ * at least 16384 shell quartets is timed, on up to 2^19 of its quartets
+ * accumulated into a scratch K, with 64, 128 and 256 threads per block and
+ * with one thread per quartet or a persistent grid of 1x or 2x the blocks
+ * that fit on an SM; the fastest shape is kept for later builds of this
+ * context.  *n_tuned = streams tuned (may be NULL). */
+int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int32_t* n_tuned);
+
+/* Current launch shape of the 162 streams (threads per block; persistent
+ * blocks per SM, 0 = one thread per quartet).  Host arrays, may be NULL. */
+int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm);
+
+/* Captured build.  kx_graph_plan runs one kx_exchange_batch build (P, K
+ * packed, K written), sizes every buffer from it with `headroom` (0.25 = 25 %
+ * more frontier tasks, leaf quartets and shell quartets per chunk than this
+ * build needed), and records a whole build of the same options into one
+ * CUDA graph in which every launch takes its sizes from device memory: the
+ * traversal and screen kernels stride over device counts with persistent
+ * grids, the class kernels read their quartet ranges from the device.
+ * kx_graph_launch replays it: reads the CURRENT contents of the P array given
+ * to kx_graph_plan and overwrites that K (the addresses are part of the
+ * graph), ordered on the context's stream.  A count beyond its capacity (or
+ * quartets of a class stream that was empty in the planning build) is
+ * detected on the device, nothing is written out of bounds, and the replay
+ * returns KX_ECAPACITY with K incomplete: plan again.  No kernel of the
+ * graph waits on another block, so no replay can time out.  Any other build
+ * on the context, kx_build_schwarz or kx_build_tree discards the plan. */
+int kx_graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double headroom, kx_stats* st);
+int kx_graph_launch(kx_ctx* c, kx_stats* st);
+
 /* Number of basis functions (summed over the systems of a batch). */
 int64_t kx_n_functions(const kx_ctx* c);
 

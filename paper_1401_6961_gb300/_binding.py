@@ -22,7 +22,8 @@ ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "K
 # every entry point declared in include/kx.h
 EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
            "kx_exchange_host", "kx_create_batch", "kx_exchange_batch", "kx_exchange_batch_host",
-           "kx_packed_size", "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
+           "kx_packed_size", "kx_autotune", "kx_get_launch_shapes", "kx_graph_plan", "kx_graph_launch",
+           "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
            "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
            "kx_block_norms", "kx_mlp_infer_bf16", "kx_mlp_loss_grad", "kx_mlp_adam",
@@ -100,6 +101,10 @@ def load() -> ctypes.CDLL:
     L.kx_create_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(kx_basis), ctypes.c_int, vp]
     L.kx_exchange_batch.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.POINTER(kx_stats)]
     L.kx_exchange_batch_host.argtypes = [vp, _f64p, ctypes.POINTER(kx_opts), _f64p, ctypes.POINTER(kx_stats)]
+    L.kx_autotune.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.POINTER(kx_stats), _i32p]
+    L.kx_get_launch_shapes.argtypes = [vp, _i32p, _i32p]
+    L.kx_graph_plan.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.c_double, ctypes.POINTER(kx_stats)]
+    L.kx_graph_launch.argtypes = [vp, ctypes.POINTER(kx_stats)]
     L.kx_packed_size.argtypes = [vp]
     L.kx_packed_size.restype = ctypes.c_int64
     L.kx_n_functions.argtypes = [vp]
@@ -205,6 +210,34 @@ def kx_exchange_batch_host(ctx, P: np.ndarray, opts: kx_opts, K: np.ndarray) -> 
 
 def kx_packed_size(ctx) -> int:
     return int(load().kx_packed_size(ctx))
+
+
+def kx_autotune(ctx, P_ptr: int, opts: kx_opts, K_ptr: int) -> Tuple[kx_stats, int]:
+    st = kx_stats()
+    n = ctypes.c_int32()
+    _check(ctx, load().kx_autotune(ctx, ctypes.c_void_p(P_ptr), ctypes.byref(opts), ctypes.c_void_p(K_ptr),
+                                   ctypes.byref(st), ctypes.byref(n)))
+    return st, int(n.value)
+
+
+def kx_get_launch_shapes(ctx) -> Tuple[np.ndarray, np.ndarray]:
+    t = np.zeros(162, dtype=np.int32)
+    b = np.zeros(162, dtype=np.int32)
+    _check(ctx, load().kx_get_launch_shapes(ctx, _p(t, _i32p), _p(b, _i32p)))
+    return t, b
+
+
+def kx_graph_plan(ctx, P_ptr: int, opts: kx_opts, K_ptr: int, headroom: float = 0.25) -> kx_stats:
+    st = kx_stats()
+    _check(ctx, load().kx_graph_plan(ctx, ctypes.c_void_p(P_ptr), ctypes.byref(opts), ctypes.c_void_p(K_ptr),
+                                     float(headroom), ctypes.byref(st)))
+    return st
+
+
+def kx_graph_launch(ctx) -> kx_stats:
+    st = kx_stats()
+    _check(ctx, load().kx_graph_launch(ctx, ctypes.byref(st)))
+    return st
 
 
 def kx_build_schwarz(ctx, tau_ovlp: float = 0.0) -> None:
@@ -495,6 +528,24 @@ class BatchExchange:
         K = np.zeros_like(P)
         self.stats = kx_exchange_batch_host(self.ctx, np.ascontiguousarray(P), kx_default_opts(**opts), K)
         return K
+
+    def autotune(self, P, out=None, **opts):
+        """One build that also tunes the class kernels' launch shapes."""
+        import torch
+        K = out if out is not None else torch.empty_like(P)
+        self.stats, self.n_tuned = kx_autotune(self.ctx, P.data_ptr(), kx_default_opts(**opts), K.data_ptr())
+        return K
+
+    def plan(self, P, K, headroom: float = 0.25, **opts):
+        """Captures a build reading P and writing K (static buffers) into a
+        CUDA graph; ``replay()`` then rebuilds K from P's current contents."""
+        self.stats = kx_graph_plan(self.ctx, P.data_ptr(), kx_default_opts(**opts), K.data_ptr(), headroom)
+        self._graph_bufs = (P, K)
+        return K
+
+    def replay(self):
+        self.stats = kx_graph_launch(self.ctx)
+        return self._graph_bufs[1]
 
     def worklist(self) -> np.ndarray:
         return kx_get_worklist(self.ctx)

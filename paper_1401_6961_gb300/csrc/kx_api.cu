@@ -42,13 +42,18 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 int check_ctx(const kx_ctx* c) { return c ? KX_OK : KX_EINVAL; }
 
 void free_all(kx_ctx* c) {
+    drop_graph(c);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->h_gw) cudaFreeHost(c->h_gw);
+    c->gstream = nullptr;
+    c->h_gw = nullptr;
     void* ptrs[] = {c->d_tl, c->d_tctr, c->d_talpha, c->d_tfoff, c->d_perm, c->d_s2, c->d_snorm, c->d_slog,
                     c->d_pq, c->d_pnorm, c->d_plog, c->d_node_lo, c->d_node_hi, c->d_node_child,
                     c->d_node_nchild, c->d_sq_s, c->d_sq_p, c->d_nrm_s, c->d_nrm_p, c->d_leaf_lo, c->d_leaf_hi,
                     c->d_boys64, c->d_boys32, c->d_pairmap, c->d_scratch, c->d_front[0], c->d_front[1],
                     c->d_mask, c->d_scan, c->d_rec, c->d_bin, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
                     c->d_hostP, c->d_hostK, c->d_leafdesc, c->d_list, c->d_sseg, c->d_tsys, c->d_lseg,
-                    c->d_node_sys, c->d_mframe};
+                    c->d_node_sys, c->d_mframe, c->d_gw, c->d_groots, c->d_gactive, c->d_tuneK};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < NPAIRCLASS; ++i) {
@@ -179,6 +184,7 @@ int kx_build_schwarz(kx_ctx* c, double tau_ovlp) {
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
     c->tau_ovlp = tau_ovlp;
     c->have_tree = false;
+    drop_graph(c);
     return schwarz(c, tau_ovlp);
 }
 
@@ -209,6 +215,7 @@ int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm) {
     }
     c->have_tree = false;
     c->keep_valid = false;
+    drop_graph(c);
     return build_tree(c, leaf_max_functions);
 }
 
@@ -316,6 +323,61 @@ int kx_exchange_batch_host(kx_ctx* c, const double* P_host, const kx_opts* o, do
     KX_CUDA(c, cudaMemcpyAsync(K_host, c->d_hostK, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     KX_CUDA(c, cudaStreamSynchronize(c->stream));
     return KX_OK;
+}
+
+int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int32_t* n_tuned) {
+    KX_TRY(check_ctx(c));
+    if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
+    if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
+    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    kx_stats local;
+    kx_stats* s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
+    int n = 0;
+    int r = autotune(c, P, o, K, s, &n);
+    if (n_tuned) *n_tuned = n;
+    return r;
+}
+
+int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm) {
+    if (!c) return KX_EINVAL;
+    for (int s = 0; s < 2 * NCLASS; ++s) {
+        if (threads) threads[s] = c->eri_threads[s];
+        if (blocks_per_sm) blocks_per_sm[s] = c->eri_bpsm[s];
+    }
+    return KX_OK;
+}
+
+int kx_graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double headroom, kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
+    if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
+    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
+        return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
+    if (!std::isfinite(headroom) || headroom < 0.0 || headroom > 16.0)
+        return set_err(c, KX_EINVAL, "headroom must be in [0, 16]");
+    if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    kx_stats local;
+    kx_stats* s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
+    return graph_plan(c, P, o, K, headroom, s);
+}
+
+int kx_graph_launch(kx_ctx* c, kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    return graph_launch(c, st);
 }
 
 int64_t kx_n_functions(const kx_ctx* c) { return c ? c->n_fn : -1; }

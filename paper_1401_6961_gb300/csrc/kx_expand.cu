@@ -31,6 +31,7 @@ constexpr float LOG_MARGIN = 1e-3f;   // log2 units; FP32 error of the sum < 6e-
 struct ExpandArgs {
     const Task* leaves;
     int64_t n;
+    const int64_t* dn;       // device count (n is then a capacity), may be null
     const int32_t* llo;
     const int32_t* lhi;
     const int32_t* tl;
@@ -139,7 +140,8 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long ncand = 0;
-    for (int64_t q = warp; q < p.n; q += nwarp) {
+    const int64_t nq = p.dn ? min(p.n, *p.dn) : p.n;
+    for (int64_t q = warp; q < nq; q += nwarp) {
         const Task t = p.leaves[q];
         const int a0 = p.llo[t.a], na = p.lhi[t.a] - a0;
         const int b0 = p.llo[t.b], nb = p.lhi[t.b] - b0;
@@ -264,6 +266,7 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
     ExpandArgs a;
     a.leaves = leaves;
     a.n = n;
+    a.dn = nullptr;
     a.llo = c->d_leaf_lo;
     a.lhi = c->d_leaf_hi;
     a.tl = c->d_tl;
@@ -306,6 +309,29 @@ int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
     k_expand<true><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
                                                                       c->d_counters + CTR_END,
                                                                       c->d_counters + CTR_ERR);
+    return KX_OK;
+}
+
+int expand_count_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* dn, double tau, double split,
+                     int mixed, int shell_screen, int64_t* bin) {
+    if (cap <= 0) return KX_OK;
+    ExpandArgs a = make_args(c, leaves, cap, tau, split, mixed, shell_screen);
+    a.dn = dn;
+    k_expand<false><<<expand_grid(cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+                                                                         nullptr, nullptr);
+    c->launches++;
+    return KX_OK;
+}
+
+int expand_write_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* dn, double tau, double split,
+                     int mixed, int shell_screen, int64_t* bin_off, Quartet* rec) {
+    if (cap <= 0) return KX_OK;
+    ExpandArgs a = make_args(c, leaves, cap, tau, split, mixed, shell_screen);
+    a.dn = dn;
+    k_expand<true><<<expand_grid(cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
+                                                                        c->d_counters + CTR_END,
+                                                                        c->d_counters + CTR_ERR);
+    c->launches++;
     return KX_OK;
 }
 

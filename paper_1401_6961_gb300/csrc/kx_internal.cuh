@@ -265,6 +265,27 @@ struct kx_ctx {
     int eri_threads[2 * kx::NCLASS] = {};
     int eri_bpsm[2 * kx::NCLASS] = {};
     int n_sm = 0;
+    bool tuned[2 * kx::NCLASS] = {};
+    // what the last eager build saw (sizes for a captured plan)
+    int64_t plan_max_rec = 0;             // largest record count of one leaf chunk
+    uint8_t plan_active[2 * kx::NCLASS] = {};
+    // autotuning inside an eager build (kx_autotune)
+    bool tuning = false;
+    double* d_tuneK = nullptr;
+    size_t tuneK_cap = 0;
+    // captured build (kx_graph_plan / kx_graph_launch)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_valid = false;
+    int64_t graph_launches = 0;
+    int graph_depth = 0;
+    int64_t* d_gw = nullptr;              // device words of the captured build
+    int64_t* h_gw = nullptr;              // pinned host copy of its statistics
+    size_t gw_n = 0;
+    kx::Task* d_groots = nullptr;
+    uint8_t* d_gactive = nullptr;
+    int64_t graph_st0 = 0;                // statistics block in d_gw
+    cudaStream_t gstream = nullptr;       // capture and replay stream
     // per-stream profile of the last profiled build
     double prof_ms[2 * kx::NCLASS] = {};
     int64_t prof_n[2 * kx::NCLASS] = {};
@@ -315,6 +336,7 @@ int boys_table(kx_ctx* c);                                    // kx_setup.cu
 int set_frames(kx_ctx* c, int64_t ldp, int64_t ldk, bool packed);   // kx_setup.cu
 int p_norms(kx_ctx* c, const double* P);                      // kx_setup.cu
 int pair_tables(kx_ctx* c, double tau, bool want32);          // kx_setup.cu
+int pair_tables_dev(kx_ctx* c, double tau, bool screen);      // kx_setup.cu, capture-safe
 int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);  // kx_traverse.cu
 int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
                           double* K, int64_t ldk, kx_stats* st);  // kx_traverse.cu
@@ -323,6 +345,11 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
 enum { RUN_EXCHANGE = 0, RUN_TRAVERSE = 1, RUN_EVALUATE = 2 };
 int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
           kx_stats* st, const Task* list, int64_t nlist);
+void drop_graph(kx_ctx* c);
+// captured builds and the launch-shape autotuner (kx_traverse.cu); P and K packed
+int graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double headroom, kx_stats* st);
+int graph_launch(kx_ctx* c, kx_stats* st);
+int autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int* n_tuned);
 
 // shell expansion + class kernels (kx_expand.cu, kx_eri_*.cu)
 struct ClassCounts {
@@ -337,6 +364,15 @@ int expand_count(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, do
                  int mixed, int shell_screen, int64_t* bin);
 int expand_write(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
                  int mixed, int shell_screen, int64_t* bin_off, Quartet* rec);
+// capture-safe variants: the leaf count is the device word *dn (cap bounds
+// it and fixes the grid, expand_blocks(cap))
+int expand_count_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* dn, double tau, double split,
+                     int mixed, int shell_screen, int64_t* bin);
+int expand_write_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* dn, double tau, double split,
+                     int mixed, int shell_screen, int64_t* bin_off, Quartet* rec);
+int exclusive_scan_dev(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, const int64_t* dn, int64_t* grand);
+size_t scan_scratch(int64_t n);
+
 // ERI class kernels (kx_eri_impl.cuh).  Launch shapes: any multiple of 32
 // threads up to ERI_MAX_THREADS; the grid strides over the records, so a
 // persistent grid (a few blocks per SM) and one thread per record run the

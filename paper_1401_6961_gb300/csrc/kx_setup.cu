@@ -823,9 +823,12 @@ int boys_table(kx_ctx* c) {
 // take part.
 __global__ void k_pair_flags(const Seg* __restrict__ seg, int nseg, int64_t n2, const int32_t* __restrict__ tl,
                              const double* __restrict__ snorm, const double* __restrict__ s2, double tau,
-                             double pmax, double smax, int screen, int cls, int64_t* __restrict__ flag) {
+                             const unsigned long long* __restrict__ mx, int screen, int cls,
+                             int64_t* __restrict__ flag) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n2) return;
+    // maxima of S and of the P shell-block norms (bit patterns, see k_max_reduce)
+    const double smax = __longlong_as_double((long long)mx[0]), pmax = __longlong_as_double((long long)mx[1]);
     int a, b;
     seg_pair(seg, nseg, i, a, b);
     int ok = (tl[a] * 3 + tl[b] == cls) && s2[i] > 0.0;
@@ -893,20 +896,18 @@ __global__ void k_max_reduce(const double* __restrict__ x, int64_t n, unsigned l
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-int pair_tables(kx_ctx* c, double tau, bool screen) {
-    int64_t n2 = c->sp_total;
-    // maxima of S and of the P shell-block norms
+static void pair_maxima(kx_ctx* c) {
+    const int64_t n2 = c->sp_total;
     unsigned long long* d_mx = c->d_counters;   // two slots
     cudaMemsetAsync(d_mx, 0, 2 * sizeof(unsigned long long), c->stream);
     k_max_reduce<<<1024, 256, 0, c->stream>>>(c->d_snorm, n2, d_mx);
     k_max_reduce<<<1024, 256, 0, c->stream>>>(c->d_pnorm, n2, d_mx + 1);
     c->launches += 2;
-    unsigned long long mx[2];
-    cudaMemcpyAsync(mx, d_mx, sizeof(mx), cudaMemcpyDeviceToHost, c->stream);
-    KX_CUDA(c, cudaStreamSynchronize(c->stream));
-    double smax, pmax;
-    memcpy(&smax, &mx[0], 8);
-    memcpy(&pmax, &mx[1], 8);
+}
+
+int pair_tables(kx_ctx* c, double tau, bool screen) {
+    int64_t n2 = c->sp_total;
+    pair_maxima(c);
     if (!c->d_pairmap) KX_CUDA(c, cudaMalloc(&c->d_pairmap, sizeof(int32_t) * n2));
     KX_TRY(grow(c, &c->d_scan, &c->scan_cap, (size_t)2 * n2 + 16));
     int64_t* flag = c->d_scan;
@@ -914,8 +915,8 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
     unsigned g = (unsigned)((n2 + 255) / 256);
     for (int cls = 0; cls < NPAIRCLASS; ++cls) {
         int la = cls / 3, lb = cls % 3;
-        k_pair_flags<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, c->d_tl, c->d_snorm, c->d_s2, tau, pmax,
-                                               smax, screen ? 1 : 0, cls, flag);
+        k_pair_flags<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, c->d_tl, c->d_snorm, c->d_s2, tau,
+                                               c->d_counters, screen ? 1 : 0, cls, flag);
         int64_t total = 0;
         KX_TRY(exclusive_scan(c, flag, slot, n2, &total));
         c->n_pairs[cls] = total;
@@ -934,6 +935,30 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
             }
             c->pair_cap[cls] = (int64_t)cap;
         }
+        k_pair_fill<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, cls, c->d_tl, c->d_tctr, c->d_talpha,
+                                              c->d_tfoff, c->d_mframe, flag, slot, c->d_pairmap, c->d_pairmeta[cls],
+                                              c->d_pair64[cls], c->d_pair32[cls]);
+        c->launches += 2;
+    }
+    return KX_OK;
+}
+
+// Capture-safe: no host read-back.  The tables must already hold every pair
+// of nonzero Schwarz factor (pair_tables(c, 0, false) reserves that); the
+// slot bound of the class kernels is then the capacity.
+int pair_tables_dev(kx_ctx* c, double tau, bool screen) {
+    int64_t n2 = c->sp_total;
+    if (!c->d_pairmap || c->scan_cap < (size_t)2 * n2 + 16)
+        return set_err(c, KX_ESTATE, "pair tables not reserved");
+    pair_maxima(c);
+    int64_t* flag = c->d_scan;
+    int64_t* slot = c->d_scan + n2;
+    unsigned g = (unsigned)((n2 + 255) / 256);
+    for (int cls = 0; cls < NPAIRCLASS; ++cls) {
+        k_pair_flags<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, c->d_tl, c->d_snorm, c->d_s2, tau,
+                                               c->d_counters, screen ? 1 : 0, cls, flag);
+        KX_TRY(exclusive_scan_dev(c, flag, slot, n2, nullptr, (int64_t*)(c->d_counters + 2)));
+        c->n_pairs[cls] = c->pair_cap[cls];
         k_pair_fill<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, cls, c->d_tl, c->d_tctr, c->d_talpha,
                                               c->d_tfoff, c->d_mframe, flag, slot, c->d_pairmap, c->d_pairmeta[cls],
                                               c->d_pair64[cls], c->d_pair32[cls]);

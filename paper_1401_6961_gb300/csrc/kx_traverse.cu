@@ -15,6 +15,7 @@
 // of the leaf list and of the shell-quartet records made from it.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "kx_internal.cuh"
 
@@ -54,9 +55,12 @@ __device__ int64_t block_excl_scan64(int64_t v, int64_t* sh, int64_t* total) {
     return ex;
 }
 
+// n = *dn when dn is given (the grid then covers a capacity >= *dn)
 __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int64_t* __restrict__ in, int64_t n,
+                                                       const int64_t* __restrict__ dn,
                                                        int64_t* __restrict__ tile_sum) {
     __shared__ int64_t sh[32];
+    if (dn) n = min(n, *dn);
     const int64_t base = blockIdx.x * (int64_t)SCAN_TILE + threadIdx.x * (int64_t)SCAN_I;
     int64_t s = 0;
 #pragma unroll
@@ -68,9 +72,11 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int64_t* __restrict
 }
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const int64_t* __restrict__ in, int64_t n,
+                                                       const int64_t* __restrict__ dn,
                                                        const int64_t* __restrict__ tile_off,
                                                        int64_t* __restrict__ out, int64_t* __restrict__ grand) {
     __shared__ int64_t sh[32];
+    if (dn) n = min(n, *dn);
     const int64_t base = blockIdx.x * (int64_t)SCAN_TILE + threadIdx.x * (int64_t)SCAN_I;
     int64_t v[SCAN_I];
     int64_t s = 0;
@@ -99,18 +105,21 @@ static size_t scan_tmp_need(int64_t n) {
     return need;
 }
 
-static int scan_rec(cudaStream_t st, const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, int64_t* grand) {
+// dn (device, may be null) bounds the outermost level; the tile grids are
+// sized by the capacity n, entries beyond *dn count as zero
+static int scan_rec(cudaStream_t st, const int64_t* in, int64_t* out, int64_t n, const int64_t* dn, int64_t* tmp,
+                    int64_t* grand) {
     int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles <= 1) {
-        k_scan_apply<<<1, SCAN_T, 0, st>>>(in, n, nullptr, out, grand);
+        k_scan_apply<<<1, SCAN_T, 0, st>>>(in, n, dn, nullptr, out, grand);
         return 1;
     }
     int64_t* tsum = tmp;
     int64_t* toff = tmp + tiles;
     int64_t* inner_grand = tmp + 2 * tiles;
-    k_scan_tiles<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, n, tsum);
-    int k = scan_rec(st, tsum, toff, tiles, tmp + 2 * tiles + 2, inner_grand);
-    k_scan_apply<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, n, toff, out, grand);
+    k_scan_tiles<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, n, dn, tsum);
+    int k = scan_rec(st, tsum, toff, tiles, nullptr, tmp + 2 * tiles + 2, inner_grand);
+    k_scan_apply<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, n, dn, toff, out, grand);
     return k + 2;
 }
 
@@ -121,13 +130,24 @@ int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_
     }
     KX_TRY(grow(c, &c->d_scantmp, &c->scantmp_cap, scan_tmp_need(n) + 8));
     int64_t* grand = c->d_scantmp;
-    c->launches += scan_rec(c->stream, in, out, n, c->d_scantmp + 8, grand);
+    c->launches += scan_rec(c->stream, in, out, n, nullptr, c->d_scantmp + 8, grand);
     if (total_host) {
         KX_CUDA(c, cudaMemcpyAsync(total_host, grand, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
         KX_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     return KX_OK;
 }
+
+// the same without any host read-back (capture-safe): the total goes to the
+// device word *grand; the scratch must have been grown for capacity n
+int exclusive_scan_dev(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, const int64_t* dn, int64_t* grand) {
+    if (n <= 0) return KX_OK;
+    if (c->scantmp_cap < scan_tmp_need(n) + 8) return set_err(c, KX_ECAPACITY, "scan scratch not reserved");
+    c->launches += scan_rec(c->stream, in, out, n, dn, c->d_scantmp + 8, grand);
+    return KX_OK;
+}
+
+size_t scan_scratch(int64_t n) { return scan_tmp_need(n) + 8; }
 
 // ===========================================================================
 // traversal kernels
@@ -140,7 +160,8 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
                               const int32_t* __restrict__ nchild, const int32_t* __restrict__ node_sys,
                               const Seg* __restrict__ lseg_next, const double* __restrict__ S,
                               const double* __restrict__ Pn, double tau, uint16_t* __restrict__ mask,
-                              int64_t* __restrict__ cnt) {
+                              int64_t* __restrict__ cnt, const int64_t* __restrict__ dn) {
+    if (dn) n = min(n, *dn);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const Task t = front[i];
         const Seg g = lseg_next[node_sys[t.a]];
@@ -167,9 +188,17 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
     }
 }
 
+// parents [p0, p1) write their surviving children at off - obase; with
+// drange (device: p0, p1, obase) the range comes from the device
 __global__ void k_expand_write(const Task* __restrict__ front, int64_t p0, int64_t p1,
                                const uint16_t* __restrict__ mask, const int64_t* __restrict__ off, int64_t obase,
-                               const int32_t* __restrict__ child, Task* __restrict__ out) {
+                               const int32_t* __restrict__ child, Task* __restrict__ out,
+                               const int64_t* __restrict__ drange) {
+    if (drange) {
+        p0 = drange[0];
+        p1 = drange[1];
+        obase = drange[2];
+    }
     for (int64_t i = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p1;
          i += (int64_t)gridDim.x * blockDim.x) {
         unsigned m = mask[i];
@@ -230,6 +259,15 @@ __global__ void k_to_f32(const double* __restrict__ P, int64_t ldp, int64_t rows
 // driver
 // ===========================================================================
 
+void drop_graph(kx_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->graph_valid = false;
+}
+
+
 namespace {
 
 struct Timer {
@@ -270,6 +308,60 @@ struct Run {
 int process_leaves(Run& r, const Task* leaves, int64_t n);
 int finish_run(kx_ctx* c, kx_stats* st, Timer& tm, int D);
 
+// Launch-shape autotuner of one (precision, class) stream: times every
+// candidate shape on (a prefix of) the stream's records, accumulating into a
+// scratch K, and keeps the fastest.  Candidates: 64, 128 and 256 threads per
+// block, each with one thread per record or a persistent grid of 1x or 2x
+// the blocks that fit on an SM.
+constexpr int64_t TUNE_MIN = 1 << 14;      // records needed to tune a stream
+constexpr int64_t TUNE_MAX = 1 << 19;      // records timed per candidate
+int tune_stream(kx_ctx* c, int s, const Quartet* rec, int64_t i0, int64_t i1, const double* P) {
+    if (i1 - i0 < TUNE_MIN) return KX_OK;
+    const int prec = s / NCLASS, cls = s % NCLASS;
+    EriKernel k = eri_kernel(cls, prec);
+    if (!k) return set_err(c, KX_EINVAL, "bad class");
+    const int64_t j1 = std::min(i1, i0 + TUNE_MAX);
+    const EriArgs args = eri_args(c, cls, prec, rec, i0, j1, nullptr, P, c->d_tuneK);
+    cudaEvent_t e0, e1;
+    KX_CUDA(c, cudaEventCreate(&e0));
+    KX_CUDA(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bt = ERI_THREADS, bb = 0;
+    for (int threads : {64, 128, 256}) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0) != cudaSuccess || occ < 1) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        for (int bpsm : {0, occ, 2 * occ}) {
+            int64_t blocks = (j1 - i0 + threads - 1) / threads;
+            if (bpsm > 0) blocks = std::min<int64_t>(blocks, (int64_t)bpsm * c->n_sm);
+            float t = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, c->stream);
+                k<<<(unsigned)blocks, threads, 0, c->stream>>>(args);
+                cudaEventRecord(e1, c->stream);
+                KX_CUDA(c, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t += ms;   // the first launch warms the caches
+            }
+            if (t < best) {
+                best = t;
+                bt = threads;
+                bb = bpsm;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    KX_CUDA(c, cudaGetLastError());
+    c->eri_threads[s] = bt;
+    c->eri_bpsm[s] = bb;
+    c->tuned[s] = true;
+    return KX_OK;
+}
+
 // shell screen, class binning and class kernels for one list of leaf quartets
 int process_leaves(Run& r, const Task* leaves, int64_t n) {
     kx_ctx* c = r.c;
@@ -286,6 +378,7 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     c->launches++;
     int64_t total = 0;
     KX_TRY(exclusive_scan(c, bin, binoff, nbin, &total));
+    c->plan_max_rec = std::max(c->plan_max_rec, total);
     if (total > r.rec_limit && n > 1) {
         // too many records for one pass: halve the leaf list
         int64_t h0 = n / 2;
@@ -312,6 +405,8 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     for (int s = 0; s < 2 * NCLASS; ++s) {
         if (!h[s]) continue;
         const int prec = s / NCLASS, cls = s % NCLASS;
+        c->plan_active[s] = 1;
+        if (c->tuning && !c->tuned[s]) KX_TRY(tune_stream(c, s, c->d_rec, off[s], off[s + 1], r.P));
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (r.o->profile) {
             cudaEventCreate(&e0);
@@ -361,6 +456,8 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
           kx_stats* st, const Task* list, int64_t nlist) {
     const int D = c->depth;
     const bool evaluate = mode != RUN_TRAVERSE;
+    // an eager build may move the buffers a captured plan points to
+    drop_graph(c);
     Timer tm{c, {}};
     Run r{c, P, ldp, o, K, ldk, st, &tm, 0, 0.0};
     // record budget per pass: the caller's, else 2^30 records (8 GB) or a
@@ -373,7 +470,9 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     const int64_t lq_cap = std::max<int64_t>(r.rec_limit / 48, 1 << 16);
 
     c->launches = 0;
+    c->plan_max_rec = 0;
     for (int s = 0; s < 2 * NCLASS; ++s) {
+        c->plan_active[s] = 0;
         c->prof_ms[s] = 0.0;
         c->prof_n[s] = 0;
         c->prof_flops[s] = 0.0;
@@ -456,7 +555,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
             int64_t* off = c->d_scan + nfront;
             unsigned g = (unsigned)std::min<int64_t>((nfront + 255) / 256, 152 * 64);
             k_expand_mask<<<g, 256, 0, c->stream>>>(c->d_front[cur], nfront, child, nchild, nsys, lnext, S, Pn,
-                                                    o->tau, c->d_mask, cnt);
+                                                    o->tau, c->d_mask, cnt, nullptr);
             c->launches++;
             int64_t total = 0;
             KX_TRY(exclusive_scan(c, cnt, off, nfront, &total));
@@ -464,7 +563,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
             if (k + 1 < D) {
                 KX_TRY(grow(c, &c->d_front[1 - cur], &c->front_cap[1 - cur], (size_t)std::max<int64_t>(total, 1)));
                 k_expand_write<<<g, 256, 0, c->stream>>>(c->d_front[cur], 0, nfront, c->d_mask, off, 0, child,
-                                                         c->d_front[1 - cur]);
+                                                         c->d_front[1 - cur], nullptr);
                 c->launches++;
                 cur = 1 - cur;
                 nfront = total;
@@ -499,7 +598,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
                 tm.mark(ST_EXPAND);
                 unsigned g2 = (unsigned)std::min<int64_t>((p1 - p0 + 255) / 256, 152 * 64);
                 k_expand_write<<<g2, 256, 0, c->stream>>>(c->d_front[cur], p0, p1, c->d_mask, off, o0, child,
-                                                          c->d_front[1 - cur]);
+                                                          c->d_front[1 - cur], nullptr);
                 c->launches++;
                 if (keep) KX_TRY(keep_leaves(c, c->d_front[1 - cur], o1 - o0));
                 if (evaluate) KX_TRY(process_leaves(r, c->d_front[1 - cur], o1 - o0));
@@ -548,6 +647,392 @@ int finish_run(kx_ctx* c, kx_stats* st, Timer& tm, int D) {
 int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
                           kx_stats* st) {
     return drive(c, RUN_EXCHANGE, P, ldp, o, K, ldk, st, nullptr, 0);
+}
+
+// ===========================================================================
+// captured builds: every launch sized from device words, one CUDA graph
+// ===========================================================================
+//
+// A plan fixes, from an eager build of the same systems and options, the
+// capacities of every buffer (frontiers, leaf chunks, shell-quartet
+// records) with some headroom, and records the whole build -- P norms, pair
+// tables, every traversal level, every leaf chunk's screen, binning and
+// class-kernel launches -- into one CUDA graph.  No launch of the graph
+// reads a size on the host: counts live in device words (layout below), the
+// traversal and screen kernels stride over them with persistent grids, and
+// the class kernels read their record ranges from the device.  A count that
+// exceeds its capacity, or records of a class stream the plan did not
+// launch, set an overflow word instead of writing out of bounds; the host
+// checks it after the replay (KX_ECAPACITY: re-plan).  No kernel waits on
+// another block, so no device-side wait exists that could time out.
+
+namespace {
+
+// device words of a captured build
+struct GraphWords {
+    int D, nch;
+    int64_t n(int k) const { return k; }                    // level task counts [D + 1]
+    int64_t t(int k) const { return 32 + k; }               // level totals (scan grands) [D + 1]
+    int64_t wr(int k) const { return 64 + 3 * k; }          // write ranges of levels [D]
+    int64_t ch(int j) const { return 160 + 4 * (int64_t)j; } // chunk: p0, p1, o0, n_leaf
+    int64_t rg() const { return 160 + 4 * (int64_t)nch; }   // stream ranges [2 * 162]
+    int64_t ne() const { return rg() + 4 * NCLASS; }        // leaf count of the write pass
+    int64_t bt() const { return ne() + 1; }                 // record total of a chunk
+    int64_t st() const { return bt() + 1; }                 // statistics: records per stream [162]
+    int64_t lq() const { return st() + 2 * NCLASS; }        // leaf quartets evaluated
+    int64_t flag() const { return lq() + 1; }               // overflow
+    int64_t size() const { return flag() + 3; }             // + two read-back slots
+};
+
+// next frontier size, or 0 (and the overflow word) when it exceeds cap;
+// the write pass of the level covers its parents only when it fits
+__global__ void k_level_check(const int64_t* __restrict__ total, const int64_t* __restrict__ n_parent,
+                              int64_t cap, int64_t* __restrict__ n_next, int64_t* __restrict__ wr,
+                              int64_t* __restrict__ flag) {
+    const bool ok = *total <= cap;
+    *n_next = ok ? *total : 0;
+    wr[0] = 0;
+    wr[1] = ok ? *n_parent : 0;
+    wr[2] = 0;
+    if (!ok) *flag = 1;
+}
+
+// chunk j of the last level: parents [p0, p1) whose children fill the
+// leaf-quartet slots [j * lq, (j + 1) * lq) (rounded to whole parents)
+__global__ void k_chunk_dev(const int64_t* __restrict__ off, const int64_t* __restrict__ n_parent,
+                            const int64_t* __restrict__ total, int64_t lq, int j, int nch,
+                            int64_t* __restrict__ ch, int64_t* __restrict__ flag) {
+    const int64_t n = *n_parent, tot = *total;
+    if (j == 0 && tot > (int64_t)nch * lq) *flag = 1;
+    auto first_at = [&](int64_t target) {   // first parent with off >= target
+        int64_t a = 0, b = n;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (off[m] < target) a = m + 1; else b = m;
+        }
+        return a;
+    };
+    const int64_t p0 = first_at((int64_t)j * lq);
+    const int64_t p1 = (j + 1 == nch) ? n : first_at((int64_t)(j + 1) * lq);
+    const int64_t o0 = p0 < n ? off[p0] : tot, o1 = p1 < n ? off[p1] : tot;
+    const bool ok = tot <= (int64_t)nch * lq && o1 - o0 <= lq + 16;
+    ch[0] = p0;
+    ch[1] = ok ? p1 : p0;
+    ch[2] = o0;
+    ch[3] = ok ? o1 - o0 : 0;
+    if (!ok) *flag = 1;
+}
+
+// record ranges of the chunk's class streams from the scanned bins; records
+// beyond the capacity, or of a stream without a captured launch, void the
+// chunk (the overflow word is set)
+__global__ void k_stream_setup(const int64_t* __restrict__ binoff, int nb, const int64_t* __restrict__ total,
+                               int64_t rec_cap, const uint8_t* __restrict__ active,
+                               const int64_t* __restrict__ n_leaf, int64_t* __restrict__ ranges,
+                               unsigned long long* __restrict__ end, int64_t* __restrict__ stats,
+                               int64_t* __restrict__ n_eff, int64_t* __restrict__ lq_total,
+                               int64_t* __restrict__ flag) {
+    const int64_t tot = *total;
+    bool ok = tot <= rec_cap;
+    for (int s = threadIdx.x; s < 2 * NCLASS; s += blockDim.x) {
+        const int64_t a = binoff[(int64_t)s * nb], b = s + 1 < 2 * NCLASS ? binoff[(int64_t)(s + 1) * nb] : tot;
+        if (b > a && !active[s]) ok = false;
+    }
+    ok = __syncthreads_and(ok);
+    for (int s = threadIdx.x; s < 2 * NCLASS; s += blockDim.x) {
+        const int64_t a = binoff[(int64_t)s * nb], b = s + 1 < 2 * NCLASS ? binoff[(int64_t)(s + 1) * nb] : tot;
+        ranges[2 * s] = ok ? a : 0;
+        ranges[2 * s + 1] = ok ? b : 0;
+        end[s] = ok ? (unsigned long long)b : 0ull;
+        if (ok) stats[s] += b - a;
+    }
+    if (threadIdx.x == 0) {
+        *n_eff = ok ? *n_leaf : 0;
+        if (ok) *lq_total += *n_leaf;
+        else *flag = 1;
+    }
+}
+
+struct GraphCaps {
+    int64_t fcap, mcap, lq, rec, nch;
+};
+
+// the screen, binning and class launches of one leaf list (capture-safe)
+int chunk_dev(kx_ctx* c, const kx_opts* o, const GraphWords& W, const GraphCaps& cap, const Task* leaves,
+              int64_t leaf_cap, const int64_t* dn, const double* P, double* K) {
+    const int mixed = o->precision == KX_MIXED;
+    const double split = mixed ? o->split_threshold : 0.0;
+    const unsigned nb = expand_blocks(leaf_cap);
+    const int64_t nbin = (int64_t)2 * NCLASS * nb;
+    int64_t* bin = c->d_bin;
+    int64_t* binoff = c->d_bin + nbin;
+    int64_t* w = c->d_gw;
+    KX_TRY(expand_count_dev(c, leaves, leaf_cap, dn, o->tau, split, mixed, o->shell_screen, bin));
+    KX_TRY(exclusive_scan_dev(c, bin, binoff, nbin, nullptr, w + W.bt()));
+    k_stream_setup<<<1, 256, 0, c->stream>>>(binoff, (int)nb, w + W.bt(), cap.rec, c->d_gactive, dn, w + W.rg(),
+                                            c->d_counters + CTR_END, w + W.st(), w + W.ne(), w + W.lq(),
+                                            w + W.flag());
+    c->launches++;
+    KX_TRY(expand_write_dev(c, leaves, leaf_cap, w + W.ne(), o->tau, split, mixed, o->shell_screen, binoff,
+                            c->d_rec));
+    for (int s = 0; s < 2 * NCLASS; ++s) {
+        if (!c->plan_active[s]) continue;
+        KX_TRY(eri_launch(c, s % NCLASS, s / NCLASS, c->d_rec, 0, 0, w + W.rg() + 2 * s, P, K));
+        c->launches++;
+    }
+    return KX_OK;
+}
+
+int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const GraphWords& W,
+                  const GraphCaps& cap) {
+    const int D = c->depth, ny = c->n_sys;
+    int64_t* w = c->d_gw;
+    const int64_t mat_total = c->sys_mat[ny];
+    // statistics and overflow words, device counters
+    KX_CUDA(c, cudaMemsetAsync(w + W.t(0), 0, sizeof(int64_t) * 32, c->stream));
+    KX_CUDA(c, cudaMemsetAsync(w + W.st(), 0, sizeof(int64_t) * (W.size() - W.st()), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(K, 0, sizeof(double) * mat_total, c->stream));
+    KX_TRY(p_norms(c, P));
+    if (o->precision == KX_MIXED) {
+        k_to_f32<<<1024, 256, 0, c->stream>>>(P, 0, 1, mat_total, c->d_P32);
+        c->launches++;
+    }
+    KX_TRY(pair_tables_dev(c, o->tau, o->shell_screen != 0));
+    const double* S = c->d_nrm_s;
+    const double* Pn = c->d_nrm_p;
+    if (D == 0) {
+        k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], w + W.t(0));
+        c->launches++;
+        return chunk_dev(c, o, W, cap, c->d_front[0], ny, w + W.t(0), P, K);
+    }
+    const Task* front = c->d_groots;
+    int cur = 0;
+    const int64_t* dn = w + W.n(0);
+    int64_t* cnt = c->d_scan;
+    int64_t* off = c->d_scan + cap.mcap;
+    const unsigned g = (unsigned)std::min<int64_t>((cap.mcap + 255) / 256, (int64_t)c->n_sm * 16);
+    for (int k = 0; k < D; ++k) {
+        const int32_t* child = c->d_node_child + c->levels[k].off;
+        const int32_t* nchild = c->d_node_nchild + c->levels[k].off;
+        const int32_t* nsys = c->d_node_sys + c->levels[k].off;
+        const Seg* lnext = c->d_lseg + (size_t)(k + 1) * ny;
+        k_expand_mask<<<g, 256, 0, c->stream>>>(front, cap.mcap, child, nchild, nsys, lnext, S, Pn, o->tau,
+                                                c->d_mask, cnt, dn);
+        c->launches++;
+        KX_TRY(exclusive_scan_dev(c, cnt, off, cap.mcap, dn, w + W.t(k + 1)));
+        if (k + 1 < D) {
+            k_level_check<<<1, 1, 0, c->stream>>>(w + W.t(k + 1), dn, cap.fcap, w + W.n(k + 1), w + W.wr(k),
+                                                  w + W.flag());
+            k_expand_write<<<g, 256, 0, c->stream>>>(front, 0, 0, c->d_mask, off, 0, child, c->d_front[cur],
+                                                     w + W.wr(k));
+            c->launches += 2;
+            front = c->d_front[cur];
+            cur = 1 - cur;
+            dn = w + W.n(k + 1);
+            continue;
+        }
+        // last level, in chunks of cap.lq leaf quartets
+        Task* leaves = c->d_front[cur];
+        for (int j = 0; j < cap.nch; ++j) {
+            k_chunk_dev<<<1, 1, 0, c->stream>>>(off, dn, w + W.t(D), cap.lq, j, (int)cap.nch, w + W.ch(j),
+                                                w + W.flag());
+            k_expand_write<<<g, 256, 0, c->stream>>>(front, 0, 0, c->d_mask, off, 0, child, leaves, w + W.ch(j));
+            c->launches += 2;
+            KX_TRY(chunk_dev(c, o, W, cap, leaves, cap.lq + 16, w + W.ch(j) + 3, P, K));
+        }
+    }
+    return KX_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// reserves every buffer of a plan at its capacity and records the graph
+int capture_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, const GraphCaps& cap) {
+    const int D = c->depth, ny = c->n_sys;
+    GraphWords W{D, (int)cap.nch};
+    const unsigned nb = expand_blocks(cap.lq + 16);
+    const int64_t nbin = (int64_t)2 * NCLASS * nb;
+    const int64_t fcap = std::max<int64_t>({cap.fcap, cap.lq + 16, (int64_t)ny + 16});
+    KX_TRY(grow(c, &c->d_front[0], &c->front_cap[0], (size_t)fcap));
+    KX_TRY(grow(c, &c->d_front[1], &c->front_cap[1], (size_t)fcap));
+    KX_TRY(grow(c, &c->d_mask, &c->mask_cap, (size_t)cap.mcap));
+    KX_TRY(grow(c, &c->d_scan, &c->scan_cap, (size_t)std::max<int64_t>(2 * cap.mcap, 2 * c->sp_total + 16)));
+    KX_TRY(grow(c, &c->d_bin, &c->bin_cap, (size_t)(2 * nbin)));
+    KX_TRY(grow(c, &c->d_rec, &c->rec_cap, (size_t)cap.rec));
+    KX_TRY(grow(c, &c->d_scantmp, &c->scantmp_cap,
+                scan_scratch(std::max<int64_t>({cap.mcap, nbin, c->sp_total}))));
+    if (o->precision == KX_MIXED) KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)c->sys_mat[ny]));
+    if (c->gw_n < (size_t)W.size()) {
+        cudaFree(c->d_gw);
+        cudaFreeHost(c->h_gw);
+        c->d_gw = nullptr;
+        c->h_gw = nullptr;
+        c->gw_n = 0;
+        KX_CUDA(c, cudaMalloc(&c->d_gw, sizeof(int64_t) * W.size()));
+        KX_CUDA(c, cudaMallocHost(&c->h_gw, sizeof(int64_t) * W.size()));
+        c->gw_n = (size_t)W.size();
+    }
+    if (!c->d_gactive) KX_CUDA(c, cudaMalloc(&c->d_gactive, 2 * NCLASS));
+    cudaFree(c->d_groots);
+    c->d_groots = nullptr;
+    KX_CUDA(c, cudaMalloc(&c->d_groots, sizeof(Task) * ny));
+    {
+        std::vector<Task> roots(ny);
+        for (int y = 0; y < ny; ++y) roots[y] = Task{(uint16_t)y, (uint16_t)y, (uint16_t)y, (uint16_t)y};
+        std::vector<int64_t> n0(32, 0);
+        n0[0] = ny;
+        KX_CUDA(c, cudaMemcpy(c->d_groots, roots.data(), sizeof(Task) * ny, cudaMemcpyHostToDevice));
+        KX_CUDA(c, cudaMemcpy(c->d_gw, n0.data(), sizeof(int64_t) * 32, cudaMemcpyHostToDevice));
+        KX_CUDA(c, cudaMemcpy(c->d_gactive, c->plan_active, 2 * NCLASS, cudaMemcpyHostToDevice));
+    }
+    KX_TRY(set_frames(c, 0, 0, true));
+    if (!c->gstream) KX_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    // record on the capture stream (the legacy default stream cannot be captured)
+    c->launches = 0;
+    cudaStream_t saved = c->stream;
+    c->stream = c->gstream;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->stream = saved;
+        return cuda_check(c, e, "begin capture");
+    }
+    int r = capture_build(c, P, o, K, W, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->stream, &g);
+    c->stream = saved;
+    if (r != KX_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "stream capture");
+    c->graph = g;
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) {
+        drop_graph(c);
+        return cuda_check(c, e, "graph instantiation");
+    }
+    c->graph_launches = c->launches;
+    c->graph_depth = D;
+    c->graph_st0 = W.st();
+    c->graph_valid = true;
+    return KX_OK;
+}
+
+}  // namespace
+
+int graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double headroom, kx_stats* st) {
+    // the eager build: K, and the sizes the plan needs
+    kx_opts oe = *o;
+    oe.keep_worklist = 0;
+    oe.profile = 0;
+    KX_TRY(drive(c, RUN_EXCHANGE, P, 0, &oe, K, 0, st, nullptr, 0));
+    const int D = c->depth, ny = c->n_sys;
+    const double m = 1.0 + headroom;
+    int64_t maxlev = 0, maxpar = ny;
+    for (int k = 1; k < D; ++k) maxlev = std::max<int64_t>(maxlev, st->n_tasks[k]);
+    for (int k = 0; k < D; ++k) maxpar = std::max<int64_t>(maxpar, st->n_tasks[k]);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const int64_t rec_limit = std::min<int64_t>((int64_t)1 << 30, (int64_t)(fr / 4 / sizeof(Quartet)));
+    // records of one chunk: the class-kernel slots are 32-bit, and the
+    // records should leave most of the memory to the rest
+    const int64_t budget = std::min<int64_t>(((int64_t)1 << 31) - 8192, (int64_t)(0.4 * fr / sizeof(Quartet)));
+    GraphCaps cap;
+    cap.lq = std::max<int64_t>(rec_limit / 48, 1 << 16);   // the eager build's chunks
+    cap.fcap = (int64_t)(maxlev * m) + 64;
+    cap.mcap = (int64_t)(maxpar * m) + 64;
+    const double need = c->plan_max_rec * m + 4096;
+    if (need <= (double)budget) {
+        cap.rec = (int64_t)need;
+    } else {
+        // smaller chunks than the eager build's, sized from its densest chunk
+        // with a margin for uneven chunks; the check replay below confirms
+        cap.lq = std::max<int64_t>(1 << 16, (int64_t)(cap.lq * (double)budget / need * 0.8));
+        cap.rec = budget;
+    }
+    KX_TRY(pair_tables(c, 0.0, false));   // reserve every pair of nonzero Schwarz factor
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        cap.nch = std::max<int64_t>(1, (int64_t)std::ceil(st->n_tasks[D] * m / (double)cap.lq));
+        if (cap.nch > 4096) return set_err(c, KX_ECAPACITY, "too many leaf chunks for a captured build");
+        KX_TRY(capture_plan(c, P, o, K, cap));
+        // a replay on the planning P must fit its own plan
+        kx_stats chk;
+        const int r = graph_launch(c, &chk);
+        if (r == KX_OK) return KX_OK;
+        if (r != KX_ECAPACITY) return r;
+        drop_graph(c);
+        cap.lq = std::max<int64_t>(1 << 16, cap.lq / 2);
+    }
+    return set_err(c, KX_ECAPACITY, "no chunk size fits the records of a leaf chunk");
+}
+
+int graph_launch(kx_ctx* c, kx_stats* st) {
+    if (!c->graph_valid) return set_err(c, KX_ESTATE, "no captured build (kx_graph_plan)");
+    // statistics block: records per stream [162], leaf quartets, overflow
+    const int64_t nstat = 2 * NCLASS + 2;
+    const int64_t st0 = c->graph_st0;
+    // the graph runs on the context's capture stream, ordered after and
+    // before the work of the context's own stream
+    cudaStream_t gs = c->gstream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    cudaStreamWaitEvent(gs, e0, 0);
+    KX_CUDA(c, cudaGraphLaunch(c->gexec, gs));
+    cudaEventRecord(e1, gs);
+    cudaStreamWaitEvent(c->stream, e1, 0);
+    KX_CUDA(c, cudaMemcpyAsync(c->h_gw, c->d_gw, sizeof(int64_t) * 64, cudaMemcpyDeviceToHost, gs));
+    KX_CUDA(c, cudaMemcpyAsync(c->h_gw + st0, c->d_gw + st0, sizeof(int64_t) * nstat, cudaMemcpyDeviceToHost, gs));
+    KX_CUDA(c, cudaMemcpyAsync(c->h_gw + st0 + nstat, c->d_counters + CTR_CAND, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, gs));
+    KX_CUDA(c, cudaMemcpyAsync(c->h_gw + st0 + nstat + 1, c->d_counters + CTR_ERR, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, gs));
+    cudaError_t e = cudaStreamSynchronize(gs);
+    const int64_t cand = c->h_gw[st0 + nstat], werr = c->h_gw[st0 + nstat + 1];
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        const int D = c->graph_depth;
+        for (int k = 0; k <= D && k < 32; ++k) st->n_tasks[k] = k == 0 ? c->h_gw[0] : c->h_gw[32 + k];
+        st->depth = D;
+        for (int s = 0; s < 2 * NCLASS; ++s) {
+            st->n_shell_quartets += c->h_gw[st0 + s];
+            if (s < NCLASS) st->n_shell_quartets_fp64 += c->h_gw[st0 + s];
+        }
+        st->n_leaf_quartets = c->h_gw[st0 + 2 * NCLASS];
+        st->n_candidates = (int64_t)cand;
+        st->n_launches = (int32_t)c->graph_launches;
+        st->ms_total = ms;
+        for (int s = 0; s < 2 * NCLASS; ++s) {
+            const double f = class_flops(s % NCLASS) * (double)c->h_gw[st0 + s];
+            if (s < NCLASS) st->flops_fp64 += f; else st->flops_fp32 += f;
+        }
+    }
+    if (c->h_gw[st0 + 2 * NCLASS + 1]) return set_err(c, KX_ECAPACITY, "a count exceeded the captured plan: re-plan");
+    if (werr) return set_err(c, KX_ECUDA, "shell-quartet count and write passes disagree");
+    return KX_OK;
+}
+
+int autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int* n_tuned) {
+    KX_TRY(grow(c, &c->d_tuneK, &c->tuneK_cap, (size_t)c->sys_mat[c->n_sys]));
+    for (int s = 0; s < 2 * NCLASS; ++s) c->tuned[s] = false;
+    c->tuning = true;
+    int r = drive(c, RUN_EXCHANGE, P, 0, o, K, 0, st, nullptr, 0);
+    c->tuning = false;
+    int n = 0;
+    for (int s = 0; s < 2 * NCLASS; ++s) n += c->tuned[s];
+    if (n_tuned) *n_tuned = n;
+    return r;
 }
 
 }  // namespace kx

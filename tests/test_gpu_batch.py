@@ -202,3 +202,93 @@ def test_batch256_sampled_systems(kx):
         got = Ks[y].cpu().numpy()[fr]
         assert np.abs(got - Kref[fr]).max() <= TOLMIX, (y, s.n_fn)
     bx.close()
+
+
+# ---------------------------------------------------------------------------
+# captured builds (CUDA graph replay) and the launch-shape autotuner
+# ---------------------------------------------------------------------------
+
+def test_graph_replay_matches_eager(kx, small_batch):
+    import torch
+    systems, dens = small_batch
+    bx = kx.BatchExchange(systems)
+    P = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).cuda()
+    Ke = bx(P, tau=1e-8).clone()
+    ste = bx.stats
+    K = torch.empty_like(P)
+    bx.plan(P, K, headroom=0.25, tau=1e-8)
+    assert torch.abs(K - Ke).max().item() <= 1e-12
+    K.zero_()
+    bx.replay()
+    torch.cuda.synchronize()
+    assert torch.abs(K - Ke).max().item() <= 1e-12
+    assert bx.stats.n_shell_quartets == ste.n_shell_quartets
+    assert bx.stats.n_leaf_quartets == ste.n_leaf_quartets
+    # new contents of the captured P: a slightly different density
+    dens2 = [0.9 * d for d in dens]
+    P.copy_(torch.from_numpy(np.concatenate([d.ravel() for d in dens2])))
+    bx.replay()
+    torch.cuda.synchronize()
+    for y, (s, d) in enumerate(zip(systems, dens2)):
+        Kref, *_ = oracle.exchange_screened(s, d, 1e-8)
+        got = K[bx.offsets[y]:bx.offsets[y + 1]].cpu().numpy().reshape(Kref.shape)
+        assert np.abs(got - Kref).max() <= TOL64, s.name
+    bx.close()
+
+
+def test_graph_replay_mixed(kx, small_batch):
+    import torch
+    systems, dens = small_batch
+    bx = kx.BatchExchange(systems)
+    P = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).cuda()
+    K = torch.empty_like(P)
+    bx.plan(P, K, tau=1e-8, precision=kx.KX_MIXED, split_threshold=1e-4)
+    K.zero_()
+    bx.replay()
+    torch.cuda.synchronize()
+    for y, (s, d) in enumerate(zip(systems, dens)):
+        Kref, *_ = oracle.exchange_screened(s, d, 1e-8)
+        got = K[bx.offsets[y]:bx.offsets[y + 1]].cpu().numpy().reshape(Kref.shape)
+        assert np.abs(got - Kref).max() <= TOLMIX, s.name
+    bx.close()
+
+
+def test_graph_overflow_is_reported(kx, small_batch):
+    """A replay that needs more than the plan reserved stops at its
+    capacity checks and reports KX_ECAPACITY; a new plan then works."""
+    import torch
+    systems, dens = small_batch
+    bx = kx.BatchExchange(systems)
+    P = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).cuda()
+    K = torch.empty_like(P)
+    bx.plan(P, K, headroom=0.0, tau=1e-4)
+    P.mul_(1e3)          # larger ||P|| blocks: many more quartets survive
+    with pytest.raises(kx.KxError) as e:
+        bx.replay()
+    assert e.value.code == kx.KX_ECAPACITY
+    bx.plan(P, K, headroom=0.0, tau=1e-4)
+    Ke = K.clone()
+    K.zero_()
+    bx.replay()
+    torch.cuda.synchronize()
+    assert torch.abs(K - Ke).max().item() <= 1e-12 * max(1.0, Ke.abs().max().item())
+    bx.close()
+
+
+def test_autotune_keeps_results(kx, small_batch):
+    import torch
+    systems, dens = small_batch
+    systems = systems + [wl.water_cluster(12, 12, "small")]
+    dens = dens + [wl.density(systems[-1], 2012)]
+    bx = kx.BatchExchange(systems)
+    P = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).cuda()
+    Ke = bx(P, tau=1e-10).clone()
+    Kt = bx.autotune(P, tau=1e-10)
+    assert bx.n_tuned >= 1
+    threads, bpsm = kx.kx_get_launch_shapes(bx.ctx)
+    assert set(threads.tolist()) <= {64, 128, 256} and (bpsm >= 0).all()
+    K2 = bx(P, tau=1e-10)
+    torch.cuda.synchronize()
+    assert torch.abs(Kt - Ke).max().item() <= 1e-12
+    assert torch.abs(K2 - Ke).max().item() <= 1e-12
+    bx.close()
