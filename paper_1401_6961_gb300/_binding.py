@@ -462,6 +462,28 @@ class Exchange:
         self.stats = kx_exchange_host(self.ctx, np.ascontiguousarray(P), kx_default_opts(**opts), K)
         return K
 
+    def autotune(self, P, out=None, **opts):
+        """One build (P, K dense and contiguous) that also tunes the class
+        kernels' launch shapes for later builds."""
+        import torch
+        assert P.is_contiguous() and P.shape == (self.n_fn, self.n_fn)
+        K = out if out is not None else torch.empty_like(P)
+        self.stats, self.n_tuned = kx_autotune(self.ctx, P.data_ptr(), kx_default_opts(**opts), K.data_ptr())
+        return K
+
+    def plan(self, P, K, headroom: float = 0.25, **opts):
+        """Captures a build reading P and writing K (dense, contiguous, static
+        buffers) into a CUDA graph; ``replay()`` rebuilds K from P's current
+        contents."""
+        assert P.is_contiguous() and K.is_contiguous() and P.shape == (self.n_fn, self.n_fn) == K.shape
+        self.stats = kx_graph_plan(self.ctx, P.data_ptr(), kx_default_opts(**opts), K.data_ptr(), headroom)
+        self._graph_bufs = (P, K)
+        return K
+
+    def replay(self):
+        self.stats = kx_graph_launch(self.ctx)
+        return self._graph_bufs[1]
+
     def worklist(self, a_filter=None) -> np.ndarray:
         return kx_get_worklist(self.ctx, a_filter)
 
