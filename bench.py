@@ -203,19 +203,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(sys_, precision, name):
+def workload_config(sys_, precision, name, symmetric=True):
     nw = sys_.n_atom // 3
     return {"workload": f"(H2O){nw} water cluster at 1 g/cm^3, even-tempered medium basis "
                         f"({sys_.n_fn} functions, {sys_.n_shell} shells), tau=1e-10",
             "name": name,
             "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": 10,
             "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
-            "shell_screen": True,
+            "shell_screen": True, "symmetric": bool(symmetric),
             "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB buffer written)",
             "parallelism": "replicas"}
 
 
-def batch_config(systems, precision):
+def batch_config(systems, precision, symmetric=True):
     nw = [s.n_atom // 3 for s in systems]
     return {"workload": f"{len(systems)} independent water clusters of 4-48 molecules (drawn {min(nw)}-{max(nw)}), "
                         f"1 g/cm^3, small even-tempered basis (13 functions per water; "
@@ -223,7 +223,8 @@ def batch_config(systems, precision):
                         f"tau={BATCH_TAU:g}",
             "name": "batch256", "systems": len(systems), "tau": BATCH_TAU, "leaf_max": 10,
             "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
-            "shell_screen": True, "launch": "one captured CUDA graph per batch build (autotuned class-kernel shapes)",
+            "shell_screen": True, "symmetric": bool(symmetric),
+            "launch": "one captured CUDA graph per batch build (autotuned class-kernel shapes)",
             "l2": "inputs larger than L2 (packed P and K 297 MB each), and a 256 MB buffer written between steps",
             "parallelism": "replicas"}
 
@@ -253,7 +254,8 @@ def run_batch(args):
     Pd = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).to(dev)
     Kd = torch.empty_like(Pd)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    mixed = dict(tau=BATCH_TAU, precision=kx.KX_MIXED, split_threshold=SPLIT)
+    sym = 0 if args.no_symmetric else 1
+    mixed = dict(tau=BATCH_TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, symmetric=sym)
 
     def barrier():
         if ws > 1:
@@ -317,7 +319,7 @@ def run_batch(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.fp64_steps):
-            bx(Pd, out=Kd, tau=BATCH_TAU, precision=kx.KX_FP64)
+            bx(Pd, out=Kd, tau=BATCH_TAU, precision=kx.KX_FP64, symmetric=sym)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = max_over_ranks(e0.elapsed_time(e1)) / args.fp64_steps
@@ -348,7 +350,7 @@ def run_batch(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": batch_config(systems, "mixed"),
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": batch_config(systems, "mixed", sym),
             "quartets_per_s": ws * st.n_shell_quartets / (ms_step * 1e-3),
             "shell_quartets": st.n_shell_quartets, "leaf_quartets": st.n_leaf_quartets,
             "shell_quartets_fp64": st.n_shell_quartets_fp64,
@@ -397,8 +399,9 @@ def run_ours(args):
     Pd = torch.from_numpy(P).to(dev)
     Kd = torch.empty((n, n), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    mixed = dict(tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, profile=1)
-    plain = dict(tau=TAU, precision=kx.KX_FP64, profile=1)
+    sym = 0 if args.no_symmetric else 1
+    mixed = dict(tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, profile=1, symmetric=sym)
+    plain = dict(tau=TAU, precision=kx.KX_FP64, profile=1, symmetric=sym)
 
     def barrier():
         if ws > 1:
@@ -519,12 +522,12 @@ def run_ours(args):
     if args.e2e_steps > 0:
         Ph = torch.from_numpy(P).pin_memory().numpy()
         Kh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
-        ex.host(Ph, tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT)
+        ex.host(Ph, tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, symmetric=sym)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(tau=TAU, precision=kx.KX_MIXED,
-                                                               split_threshold=SPLIT), Kh)
+                                                               split_threshold=SPLIT, symmetric=sym), Kh)
         dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": ws * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
                "d2h_bytes_per_step": 8 * n * n}
@@ -539,7 +542,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": workload_config(sys_, "mixed", args.workload),
+            "config": workload_config(sys_, "mixed", args.workload, sym),
             "quartets_per_s": ws * quartets / (ms_step * 1e-3),
             "shell_quartets": quartets, "leaf_quartets": st.n_leaf_quartets,
             "shell_quartets_fp64": st.n_shell_quartets_fp64,
@@ -591,6 +594,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-rows", type=int, default=2, help="K-row shells per oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-symmetric", action="store_true",
+                    help="build every K block instead of the A <= C half and its mirror")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -74,6 +74,10 @@ typedef struct {
     int32_t keep_worklist;       /* 1: retain the leaf-quartet list for kx_get_worklist */
     int32_t profile;             /* 1: time every ERI class launch (see kx_get_profile) */
     int64_t chunk_records;       /* shell quartets per evaluation chunk, 0 = default */
+    int32_t symmetric;           /* 1: P is symmetric, so K = K^T: only the K blocks (A,C)
+                                    with A <= C (tree order; shells a <= c inside a
+                                    diagonal block) are built and the rest mirrored */
+    int32_t reserved;            /* 0 */
 } kx_opts;
 
 /* Counters and stage times of the last build. */
@@ -98,7 +102,7 @@ typedef struct {
 } kx_stats;
 
 /* Fills the defaults: tau = 1e-10, split 1e-5, FP64, shell screen on,
- * no worklist retention, default chunking. */
+ * no worklist retention, default chunking, no symmetry. */
 void kx_default_opts(kx_opts* o);
 
 /* Creates a context on CUDA device `device` (made current by the call) whose

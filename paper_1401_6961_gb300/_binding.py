@@ -47,7 +47,7 @@ class kx_opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("split_threshold", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("shell_screen", ctypes.c_int32),
                 ("keep_worklist", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("chunk_records", ctypes.c_int64)]
+                ("chunk_records", ctypes.c_int64), ("symmetric", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class kx_stats(ctypes.Structure):

@@ -39,6 +39,18 @@ __global__ void k_filter_work(const Task* __restrict__ w, int64_t n, const uint8
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// tree position of the shell of every function (user order), for the
+// mirror of a symmetric build
+int function_positions(kx_ctx* c) {
+    std::vector<int32_t> inv(c->n_shell), f((size_t)c->n_fn);
+    for (int i = 0; i < c->n_shell; ++i) inv[c->perm[i]] = i;
+    for (int s = 0; s < c->n_shell; ++s)
+        for (int64_t m = c->fn_off[s]; m < c->fn_off[s + 1]; ++m) f[m] = inv[s];
+    if (!c->d_ftpos) KX_CUDA(c, cudaMalloc(&c->d_ftpos, sizeof(int32_t) * c->n_fn));
+    KX_CUDA(c, cudaMemcpy(c->d_ftpos, f.data(), sizeof(int32_t) * c->n_fn, cudaMemcpyHostToDevice));
+    return KX_OK;
+}
+
 int check_ctx(const kx_ctx* c) { return c ? KX_OK : KX_EINVAL; }
 
 void free_all(kx_ctx* c) {
@@ -53,7 +65,8 @@ void free_all(kx_ctx* c) {
                     c->d_boys64, c->d_boys32, c->d_pairmap, c->d_scratch, c->d_front[0], c->d_front[1],
                     c->d_mask, c->d_scan, c->d_rec, c->d_bin, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
                     c->d_hostP, c->d_hostK, c->d_leafdesc, c->d_list, c->d_sseg, c->d_tsys, c->d_lseg,
-                    c->d_node_sys, c->d_mframe, c->d_gw, c->d_groots, c->d_gactive, c->d_tuneK};
+                    c->d_node_sys, c->d_mframe, c->d_gw, c->d_groots, c->d_gactive, c->d_tuneK,
+                    c->d_fseg, c->d_ftpos};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < NPAIRCLASS; ++i) {
@@ -77,6 +90,8 @@ void kx_default_opts(kx_opts* o) {
     o->keep_worklist = 0;
     o->profile = 0;
     o->chunk_records = 0;
+    o->symmetric = 0;
+    o->reserved = 0;
 }
 
 int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int device, void* cuda_stream) {
@@ -160,9 +175,17 @@ int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int devi
         e = cudaMemcpyAsync(c->d_sseg, c->sseg.data(), sizeof(Seg) * n_sys, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_tsys, tsys.data(), sizeof(int32_t) * c->n_shell, cudaMemcpyHostToDevice, c->stream);
+    std::vector<Seg> fseg(n_sys);
+    for (int y = 0; y < n_sys; ++y)
+        fseg[y] = Seg{c->sys_mat[y], (int32_t)c->sys_fn[y], (int32_t)(c->sys_fn[y + 1] - c->sys_fn[y])};
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_fseg, sizeof(Seg) * n_sys);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_fseg, fseg.data(), sizeof(Seg) * n_sys, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) r = cuda_check(c, e, "kx_create");
     if (r == KX_OK) r = boys_table(c);
     if (r == KX_OK) r = order_atoms(c);
+    if (r == KX_OK) r = function_positions(c);
     if (r != KX_OK) {
         free_all(c);
         delete c;
@@ -212,6 +235,7 @@ int kx_build_tree(kx_ctx* c, int32_t leaf_max_functions, const int32_t* perm) {
                                    cudaMemcpyHostToDevice, c->stream));
         // the Schwarz table is kept in tree order: rebuild it for the new order
         KX_TRY(schwarz(c, c->tau_ovlp));
+        KX_TRY(function_positions(c));
     }
     c->have_tree = false;
     c->keep_valid = false;
@@ -232,6 +256,7 @@ int exchange_impl(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, dou
     if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
         return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
     if (o->chunk_records < 0) return set_err(c, KX_EINVAL, "chunk_records must be >= 0");
+    if (o->symmetric != 0 && o->symmetric != 1) return set_err(c, KX_EINVAL, "symmetric must be 0 or 1");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");

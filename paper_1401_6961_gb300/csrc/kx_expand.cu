@@ -45,6 +45,7 @@ struct ExpandArgs {
     double tau, split;
     float ltau, lsplit;
     int mixed, screen;
+    int sym;                 // symmetric build: inside a diagonal block (A == C) only a <= c
 };
 
 __device__ __forceinline__ bool above(float x, float lthr, double thr, const double* __restrict__ snorm,
@@ -153,6 +154,7 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
         const Seg sg = p.sseg[p.tsys[a0]];
         const int64_t t0 = sg.t0();
         const int ns = sg.n;
+        const bool diag = p.sym && t.a == t.c;   // then a0 == c0
         const Div md(nd), mb(nb), mc(nc);
         if (na <= STAGE && nb <= STAGE && nc <= STAGE && nd <= STAGE && total < 65536) {
             // stage the leaf quartet's log tables and pair classes
@@ -225,8 +227,9 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const float sab = tb.sab[ia * STAGE + ib], scd = tb.scd[ic * STAGE + id];
                     const float x = sab + tb.pbd[ib * STAGE + id] + scd;
                     const int cls = tb.cab[ia * STAGE + ib] * 9 + tb.ccd[ic * STAGE + id];
-                    stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns, pab,
-                                           pcd);
+                    if (!(diag && ia > ic))
+                        stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns,
+                                               pab, pcd);
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
             }
@@ -246,7 +249,7 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const float sab = p.slog[t0 + (int64_t)a * ns + b], scd = p.slog[t0 + (int64_t)c * ns + d];
                     const float x = sab + p.plog[t0 + (int64_t)b * ns + d] + scd;
                     const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
-                    stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, t0, ns, pab, pcd);
+                    if (!(diag && a > c)) stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, t0, ns, pab, pcd);
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
             }
@@ -263,6 +266,8 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
 
 static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed,
                             int screen) {
+    // symmetric builds: the flag of the build in progress
+    const int sym = c->build_sym;
     ExpandArgs a;
     a.leaves = leaves;
     a.n = n;
@@ -283,6 +288,7 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
     a.lsplit = split > 0.0 ? (float)std::log2(split) : -INFINITY;
     a.mixed = mixed;
     a.screen = screen;
+    a.sym = sym;
     return a;
 }
 

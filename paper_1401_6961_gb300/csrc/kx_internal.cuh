@@ -163,7 +163,10 @@ struct kx_ctx {
     kx::Seg* d_lseg = nullptr;
     int32_t* d_node_sys = nullptr;              // system of every node (flat over levels)
     kx::MatFrame* d_mframe = nullptr;           // [n_sys], per build
+    kx::Seg* d_fseg = nullptr;                  // function blocks of the systems, off = packed offset
+    int32_t* d_ftpos = nullptr;                 // tree position of every function's shell (user order)
     bool packed = false;                        // the current build's P/K are packed per system
+    int build_sym = 0;                          // the current build is symmetric (kx_opts.symmetric)
 
     // basis (host copies)
     int n_atom = 0, n_shell = 0;
@@ -338,6 +341,9 @@ int p_norms(kx_ctx* c, const double* P);                      // kx_setup.cu
 int pair_tables(kx_ctx* c, double tau, bool want32);          // kx_setup.cu
 int pair_tables_dev(kx_ctx* c, double tau, bool screen);      // kx_setup.cu, capture-safe
 int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);  // kx_traverse.cu
+// K(mu,nu) = K(nu,mu) wherever the shell of mu comes after the shell of nu
+// in tree order (the half a symmetric build leaves out)
+int mirror_k(kx_ctx* c, double* K);                           // kx_traverse.cu
 int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
                           double* K, int64_t ldk, kx_stats* st);  // kx_traverse.cu
 // what one driver call does: the whole build, the traversal alone (the leaf

@@ -160,10 +160,13 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
                               const int32_t* __restrict__ nchild, const int32_t* __restrict__ node_sys,
                               const Seg* __restrict__ lseg_next, const double* __restrict__ S,
                               const double* __restrict__ Pn, double tau, uint16_t* __restrict__ mask,
-                              int64_t* __restrict__ cnt, const int64_t* __restrict__ dn) {
+                              int64_t* __restrict__ cnt, const int64_t* __restrict__ dn, int sym) {
     if (dn) n = min(n, *dn);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const Task t = front[i];
+        // symmetric build: only K blocks (A,C) with A <= C; a node left of
+        // another has all its children left of the other's
+        const bool diag = sym && t.a == t.c;
         const Seg g = lseg_next[node_sys[t.a]];
         const int64_t t0 = g.t0();
         const int nn = g.n;
@@ -177,7 +180,7 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
                 const double sab = S[t0 + (int64_t)(ca + ia) * nn + (cb + ib)];
                 for (int id = 0; id < nd; ++id) {
                     const double x = __dmul_rn(sab, Pn[t0 + (int64_t)(cb + ib) * nn + (cd + id)]);
-                    for (int ic = 0; ic < nc; ++ic) {
+                    for (int ic = diag ? ia : 0; ic < nc; ++ic) {
                         const double beta = __dmul_rn(x, S[t0 + (int64_t)(cc + ic) * nn + (cd + id)]);
                         if (beta > tau) m |= 1u << (((ia * 2 + ib) * 2 + ic) * 2 + id);
                     }
@@ -244,6 +247,24 @@ __global__ void k_chunk_bounds(const int64_t* __restrict__ off, int64_t n, int64
     bounds[j] = a;
 }
 
+// K(mu,nu) = K(nu,mu) where the shell of mu follows the shell of nu in tree
+// order: those entries were left out by a symmetric build; the ones read
+// are never written here
+__global__ void k_mirror(const Seg* __restrict__ fseg, int nsys, int64_t total, const MatFrame* __restrict__ mf,
+                         const int32_t* __restrict__ ftpos, double* __restrict__ K) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int y = seg_find(fseg, nsys, e);
+        const Seg g = fseg[y];
+        const int64_t r = e - g.off;
+        const int mu = g.base + (int)(r / g.n), nu = g.base + (int)(r % g.n);
+        if (ftpos[mu] > ftpos[nu]) {
+            const MatFrame f = mf[y];
+            K[f.k0 + (int64_t)mu * f.ldk + nu] = K[f.k0 + (int64_t)nu * f.ldk + mu];
+        }
+    }
+}
+
 // FP32 copy of P in the same layout: n rows of n entries at stride ldp
 // (a packed batch is one row of all its entries)
 __global__ void k_to_f32(const double* __restrict__ P, int64_t ldp, int64_t rows, int64_t n,
@@ -258,6 +279,14 @@ __global__ void k_to_f32(const double* __restrict__ P, int64_t ldp, int64_t rows
 // ===========================================================================
 // driver
 // ===========================================================================
+
+int mirror_k(kx_ctx* c, double* K) {
+    const int64_t total = c->sys_mat[c->n_sys];
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)c->n_sm * 32);
+    k_mirror<<<g, 256, 0, c->stream>>>(c->d_fseg, c->n_sys, total, c->d_mframe, c->d_ftpos, K);
+    c->launches++;
+    return KX_OK;
+}
 
 void drop_graph(kx_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -486,6 +515,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     // ldp = ldk = 0: P and K are packed per system
     const bool packed = ldp == 0 && ldk == 0;
     KX_TRY(set_frames(c, ldp, ldk, packed));
+    c->build_sym = o->symmetric;
     tm.mark(ST_NORMS);
     const int64_t mat_total = c->sys_mat[c->n_sys];
     if (evaluate) {
@@ -512,6 +542,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
         st->n_leaf_quartets = nlist;
         for (int64_t i0 = 0; i0 < nlist; i0 += lq_cap)
             KX_TRY(process_leaves(r, list + i0, std::min<int64_t>(lq_cap, nlist - i0)));
+        if (o->symmetric) KX_TRY(mirror_k(c, K));
         return finish_run(c, st, tm, D);
     }
 
@@ -555,7 +586,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
             int64_t* off = c->d_scan + nfront;
             unsigned g = (unsigned)std::min<int64_t>((nfront + 255) / 256, 152 * 64);
             k_expand_mask<<<g, 256, 0, c->stream>>>(c->d_front[cur], nfront, child, nchild, nsys, lnext, S, Pn,
-                                                    o->tau, c->d_mask, cnt, nullptr);
+                                                    o->tau, c->d_mask, cnt, nullptr, o->symmetric);
             c->launches++;
             int64_t total = 0;
             KX_TRY(exclusive_scan(c, cnt, off, nfront, &total));
@@ -606,6 +637,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
         }
     }
     if (keep) c->keep_valid = true;
+    if (evaluate && o->symmetric) KX_TRY(mirror_k(c, K));
     return finish_run(c, st, tm, D);
 }
 
@@ -788,6 +820,7 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
     const int D = c->depth, ny = c->n_sys;
     int64_t* w = c->d_gw;
     const int64_t mat_total = c->sys_mat[ny];
+    c->build_sym = o->symmetric;
     // statistics and overflow words, device counters
     KX_CUDA(c, cudaMemsetAsync(w + W.t(0), 0, sizeof(int64_t) * 32, c->stream));
     KX_CUDA(c, cudaMemsetAsync(w + W.st(), 0, sizeof(int64_t) * (W.size() - W.st()), c->stream));
@@ -805,7 +838,9 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
     if (D == 0) {
         k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], w + W.t(0));
         c->launches++;
-        return chunk_dev(c, o, W, cap, c->d_front[0], ny, w + W.t(0), P, K);
+        KX_TRY(chunk_dev(c, o, W, cap, c->d_front[0], ny, w + W.t(0), P, K));
+        if (o->symmetric) KX_TRY(mirror_k(c, K));
+        return KX_OK;
     }
     const Task* front = c->d_groots;
     int cur = 0;
@@ -819,7 +854,7 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
         const int32_t* nsys = c->d_node_sys + c->levels[k].off;
         const Seg* lnext = c->d_lseg + (size_t)(k + 1) * ny;
         k_expand_mask<<<g, 256, 0, c->stream>>>(front, cap.mcap, child, nchild, nsys, lnext, S, Pn, o->tau,
-                                                c->d_mask, cnt, dn);
+                                                c->d_mask, cnt, dn, o->symmetric);
         c->launches++;
         KX_TRY(exclusive_scan_dev(c, cnt, off, cap.mcap, dn, w + W.t(k + 1)));
         if (k + 1 < D) {
@@ -843,6 +878,7 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
             KX_TRY(chunk_dev(c, o, W, cap, leaves, cap.lq + 16, w + W.ch(j) + 3, P, K));
         }
     }
+    if (o->symmetric) KX_TRY(mirror_k(c, K));
     return KX_OK;
 }
 

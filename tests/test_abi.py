@@ -43,12 +43,12 @@ def test_default_opts(lib):
     import paper_1401_6961_gb300 as kx
     o = kx.kx_default_opts()
     assert o.tau == 1e-10 and o.precision == kx.KX_FP64 and o.shell_screen == 1
-    assert o.keep_worklist == 0 and o.chunk_records == 0
+    assert o.keep_worklist == 0 and o.chunk_records == 0 and o.symmetric == 0
 
 
 def test_struct_layouts_match_header(lib):
     import paper_1401_6961_gb300 as kx
-    assert ctypes.sizeof(kx.kx_opts) == 40
+    assert ctypes.sizeof(kx.kx_opts) == 48
     assert ctypes.sizeof(kx.kx_basis) == 40
     # 4 counters + 32 levels + 4 ints + 8 doubles
     assert ctypes.sizeof(kx.kx_stats) == 8 * 4 + 8 * 32 + 4 * 4 + 8 * 8
