@@ -36,7 +36,7 @@ UNIT = "K-builds/s"
 WORKLOADS = ("water64", "water16", "batch256")
 BATCH_TAU = 1e-8
 TAU = 1e-10
-SPLIT = 1e-4
+SPLIT = 5e-4          # measured max|dK| vs FP64: 3.0e-9 on (H2O)64, 1.7e-9 on the batch
 L2_FLUSH_BYTES = 256 << 20
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",

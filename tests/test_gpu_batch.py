@@ -183,11 +183,18 @@ def test_batch_argument_errors(kx, small_batch):
 # ---------------------------------------------------------------------------
 
 def test_batch256_sampled_systems(kx):
+    """Launch configuration of the benchmark: tuned shapes, captured build
+    replayed, split 5e-4, symmetric builds."""
     import torch
     systems, dens = wl.batch_workload()
     bx = kx.BatchExchange(systems)
     P = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).cuda()
-    K = bx(P, tau=1e-8, precision=kx.KX_MIXED, split_threshold=1e-4)
+    K = torch.empty_like(P)
+    opts = dict(tau=1e-8, precision=kx.KX_MIXED, split_threshold=5e-4, symmetric=1)
+    bx.autotune(P, out=K, **opts)
+    bx.plan(P, K, **opts)
+    K.zero_()
+    bx.replay()
     torch.cuda.synchronize()
     Ks = bx.unpack(K)
     nf = np.array([s.n_fn for s in systems])

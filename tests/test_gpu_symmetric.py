@@ -107,12 +107,20 @@ def test_batch_symmetric_and_graph(kx):
 
 
 def test_water64_symmetric_mixed_rows(kx):
-    """The benchmark system in the benchmark's mode: sampled K rows."""
+    """The benchmark system in the benchmark's launch configuration (tuned
+    shapes, captured build replayed, split 5e-4, symmetric): sampled K rows."""
     import torch
     sys_, P = wl.workload("water64")
     ex = kx.Exchange(sys_)
-    K = ex(torch.from_numpy(P).cuda(), tau=1e-10, precision=kx.KX_MIXED, split_threshold=1e-4,
-           symmetric=1).cpu().numpy()
+    Pd = torch.from_numpy(P).cuda()
+    Kd = torch.empty_like(Pd)
+    opts = dict(tau=1e-10, precision=kx.KX_MIXED, split_threshold=5e-4, symmetric=1)
+    ex.autotune(Pd, out=Kd, **opts)
+    ex.plan(Pd, Kd, **opts)
+    Kd.zero_()
+    ex.replay()
+    torch.cuda.synchronize()
+    K = Kd.cpu().numpy()
     rows = [int(x) for x in np.random.default_rng(65).choice(sys_.n_shell, size=3, replace=False)]
     Kref, *_ = oracle.exchange_screened(sys_, P, 1e-10, rows=rows)
     off = sys_.shell_offset
