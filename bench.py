@@ -106,6 +106,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def barrier(ws: int) -> None:
+    """All ranks meet (no-op for one rank)."""
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of every rank's x (the slowest rank's time)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units of every rank over the slowest rank's time."""
+    return ws * units_per_rank / seconds_max
+
+
 def measured_peak(name: str):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -257,18 +280,6 @@ def run_batch(args):
     sym = 0 if args.no_symmetric else 1
     mixed = dict(tau=BATCH_TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, symmetric=sym)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # set-up (untimed): launch-shape autotuning, then the captured plan
     bx.autotune(Pd, out=Kd, **mixed)
@@ -277,7 +288,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         bx.replay()
     torch.cuda.synchronize(dev)
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize(dev)
     evs = []
     with ClockSampler(local) as clk:
@@ -290,12 +301,12 @@ def run_batch(args):
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize(dev)
-    barrier()
+    barrier(ws)
     st = bx.stats
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
     ms_step = ms / args.steps
     nsys = len(systems)
-    value = ws * nsys * 1e3 / ms_step
+    value = job_rate(nsys, ws, ms_step * 1e-3)
     Kmix = Kd.clone()
 
     # per-class profile of an eager mixed build with the same launch shapes
@@ -322,7 +333,7 @@ def run_batch(args):
             bx(Pd, out=Kd, tau=BATCH_TAU, precision=kx.KX_FP64, symmetric=sym)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms64 = max_over_ranks(e0.elapsed_time(e1)) / args.fp64_steps
+        ms64 = max_over_ranks(e0.elapsed_time(e1), ws, dev) / args.fp64_steps
         diff = float((Kmix - Kd).abs().max().item())
         fp64 = {"value": ws * nsys * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
                 "warmup": 0, "launch": "eager", "quartets_per_s": ws * bx.stats.n_shell_quartets / (ms64 * 1e-3)}
@@ -333,11 +344,11 @@ def run_batch(args):
         Kh = torch.empty(Ph.shape[0], dtype=torch.float64).pin_memory().numpy()
         o = kx.kx_default_opts(**mixed)
         kx.kx_exchange_batch_host(bx.ctx, Ph, o, Kh)
-        barrier()
+        barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             kx.kx_exchange_batch_host(bx.ctx, Ph, o, Kh)
-        dt = max_over_ranks(time.perf_counter() - t0)
+        dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
         e2e = {"value": ws * nsys * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * Ph.shape[0],
                "d2h_bytes_per_step": 8 * Ph.shape[0], "launch": "eager (kx_exchange_batch_host)"}
 
@@ -403,18 +414,6 @@ def run_ours(args):
     mixed = dict(tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, profile=1, symmetric=sym)
     plain = dict(tau=TAU, precision=kx.KX_FP64, profile=1, symmetric=sym)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     def timed_steps(opts, steps):
         evs = []
@@ -448,7 +447,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         ex.replay()
     torch.cuda.synchronize(dev)
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize(dev)
     evs = []
     with ClockSampler(local) as clk:
@@ -461,11 +460,11 @@ def run_ours(args):
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize(dev)
-    barrier()
+    barrier(ws)
     st = ex.stats
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
     ms_step = ms / args.steps
-    value = ws * 1e3 / ms_step
+    value = job_rate(1, ws, ms_step * 1e-3)
     quartets = st.n_shell_quartets
     launches = int(st.n_launches) * args.steps
     Kmix = Kd.clone()
@@ -475,7 +474,7 @@ def run_ours(args):
     # and the roofline of the dominant class kernel
     torch.cuda.synchronize(dev)
     ms_e, _, prof = timed_steps(mixed, max(1, args.eager_steps))
-    ms_e = max_over_ranks(ms_e) / max(1, args.eager_steps)
+    ms_e = max_over_ranks(ms_e, ws, dev) / max(1, args.eager_steps)
     ste = ex.stats
 
     # roofline of the dominant ERI class kernel over the timed steps
@@ -506,7 +505,7 @@ def run_ours(args):
             ex.replay()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms64 = max_over_ranks(e0.elapsed_time(e1)) / args.fp64_steps
+        ms64 = max_over_ranks(e0.elapsed_time(e1), ws, dev) / args.fp64_steps
         s64 = ex.stats
         diff = float((Kmix - Kd).abs().max().item())
         fp64 = {"value": ws * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
@@ -523,12 +522,12 @@ def run_ours(args):
         Ph = torch.from_numpy(P).pin_memory().numpy()
         Kh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
         ex.host(Ph, tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, symmetric=sym)
-        barrier()
+        barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(tau=TAU, precision=kx.KX_MIXED,
                                                                split_threshold=SPLIT, symmetric=sym), Kh)
-        dt = max_over_ranks(time.perf_counter() - t0)
+        dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
         e2e = {"value": ws * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
                "d2h_bytes_per_step": 8 * n * n}
 
