@@ -22,7 +22,7 @@ ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "K
 # every entry point declared in include/kx.h
 EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
            "kx_exchange_host", "kx_create_batch", "kx_exchange_batch", "kx_exchange_batch_host",
-           "kx_packed_size", "kx_autotune", "kx_get_launch_shapes", "kx_graph_plan", "kx_graph_launch",
+           "kx_packed_size", "kx_autotune", "kx_get_launch_shapes", "kx_set_launch_shape", "kx_graph_plan", "kx_graph_launch",
            "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
            "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
@@ -102,7 +102,8 @@ def load() -> ctypes.CDLL:
     L.kx_exchange_batch.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.POINTER(kx_stats)]
     L.kx_exchange_batch_host.argtypes = [vp, _f64p, ctypes.POINTER(kx_opts), _f64p, ctypes.POINTER(kx_stats)]
     L.kx_autotune.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.POINTER(kx_stats), _i32p]
-    L.kx_get_launch_shapes.argtypes = [vp, _i32p, _i32p]
+    L.kx_get_launch_shapes.argtypes = [vp, _i32p, _i32p, _i32p]
+    L.kx_set_launch_shape.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.kx_graph_plan.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.c_double, ctypes.POINTER(kx_stats)]
     L.kx_graph_launch.argtypes = [vp, ctypes.POINTER(kx_stats)]
     L.kx_packed_size.argtypes = [vp]
@@ -220,11 +221,17 @@ def kx_autotune(ctx, P_ptr: int, opts: kx_opts, K_ptr: int) -> Tuple[kx_stats, i
     return st, int(n.value)
 
 
-def kx_get_launch_shapes(ctx) -> Tuple[np.ndarray, np.ndarray]:
+def kx_get_launch_shapes(ctx) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(threads, blocks per SM, kernel variant) of the 162 streams."""
     t = np.zeros(162, dtype=np.int32)
     b = np.zeros(162, dtype=np.int32)
-    _check(ctx, load().kx_get_launch_shapes(ctx, _p(t, _i32p), _p(b, _i32p)))
-    return t, b
+    v = np.zeros(162, dtype=np.int32)
+    _check(ctx, load().kx_get_launch_shapes(ctx, _p(t, _i32p), _p(b, _i32p), _p(v, _i32p)))
+    return t, b, v
+
+
+def kx_set_launch_shape(ctx, stream: int, threads: int, blocks_per_sm: int = 0, variant: int = 0) -> None:
+    _check(ctx, load().kx_set_launch_shape(ctx, int(stream), int(threads), int(blocks_per_sm), int(variant)))
 
 
 def kx_graph_plan(ctx, P_ptr: int, opts: kx_opts, K_ptr: int, headroom: float = 0.25) -> kx_stats:

@@ -161,6 +161,7 @@ int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int devi
     for (int s = 0; s < 2 * NCLASS; ++s) {
         c->eri_threads[s] = ERI_THREADS;
         c->eri_bpsm[s] = 0;
+        c->eri_variant[s] = 0;
     }
     if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) c->n_sm = 152;
     std::vector<int32_t> tsys(c->n_shell);
@@ -369,12 +370,26 @@ int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stat
     return r;
 }
 
-int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm) {
+int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm, int32_t* variant) {
     if (!c) return KX_EINVAL;
     for (int s = 0; s < 2 * NCLASS; ++s) {
         if (threads) threads[s] = c->eri_threads[s];
         if (blocks_per_sm) blocks_per_sm[s] = c->eri_bpsm[s];
+        if (variant) variant[s] = c->eri_variant[s];
     }
+    return KX_OK;
+}
+
+int kx_set_launch_shape(kx_ctx* c, int32_t s, int32_t threads, int32_t blocks_per_sm, int32_t variant) {
+    KX_TRY(check_ctx(c));
+    if (s < 0 || s >= 2 * NCLASS || threads < 32 || threads > ERI_MAX_THREADS || threads % 32 || blocks_per_sm < 0)
+        return set_err(c, KX_EINVAL, "bad launch shape");
+    if (variant < 0 || variant >= eri_kernel(s % NCLASS, s / NCLASS, 0).n_variants)
+        return set_err(c, KX_EINVAL, "no such kernel variant for this stream");
+    drop_graph(c);
+    c->eri_threads[s] = threads;
+    c->eri_bpsm[s] = blocks_per_sm;
+    c->eri_variant[s] = variant;
     return KX_OK;
 }
 

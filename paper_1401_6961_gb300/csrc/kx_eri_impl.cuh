@@ -840,6 +840,421 @@ __global__ void __launch_bounds__(ERI_MAX_THREADS) k_eri_rolled(EriArgs args) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32 kernel for the largest classes (L >= ROLL_L): full Hermite sets with
+// compile-time indices, Cartesian loops at run time, R and E in shared memory
+// ---------------------------------------------------------------------------
+//
+// The rolled kernel keeps T, U and R in thread-local arrays indexed at run
+// time (local memory).  Here, per (nu, lam) of order A, T_{h'} and U_h run
+// over the FULL Hermite sets of the ket and bra (no reach pruning), so every
+// index is a compile-time constant and T, U live in registers; R_{h+h'} is
+// read from the thread's slice of shared memory once per sum index
+// s = h + h' and used for every (h, h') pair with that sum.  The E tables
+// are in shared memory as well; the slices a given nu or lam needs are
+// loaded into registers first.  The extra multiply-adds on zero E entries
+// and unreachable Hermite indices cost less than the local-memory traffic
+// they replace.  Shared memory: per thread nherm(L) + 3 etab(la,lb) +
+// 3 etab(lc,ld) floats, interleaved across the block (entry j of thread t at
+// j * blockDim + t) so that a warp's accesses fall in distinct banks.
+
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr int big_slice() {
+    return nherm(LA + LB + LC + LD) + 3 * etab(LA, LB) + 3 * etab(LC, LD);
+}
+
+template <int L>
+__device__ __forceinline__ void hermite_r_shared(float* Rs, int st, const float* G, float X, float Y, float Z) {
+    Rs[0] = G[L];
+#pragma unroll 1
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll 1
+        for (int j = L - n; j >= 1; --j)
+#pragma unroll 1
+            for (int t = j; t >= 0; --t)
+#pragma unroll 1
+                for (int u = j - t; u >= 0; --u) {
+                    const int v = j - t - u;
+                    float r;
+                    if (t > 0) {
+                        r = X * Rs[hidx(t - 1, u, v) * st];
+                        if (t > 1) r += float(t - 1) * Rs[hidx(t - 2, u, v) * st];
+                    } else if (u > 0) {
+                        r = Y * Rs[hidx(t, u - 1, v) * st];
+                        if (u > 1) r += float(u - 1) * Rs[hidx(t, u - 2, v) * st];
+                    } else {
+                        r = Z * Rs[hidx(t, u, v - 1) * st];
+                        if (v > 1) r += float(v - 1) * Rs[hidx(t, u, v - 2) * st];
+                    }
+                    Rs[hidx(t, u, v) * st] = r;
+                }
+        Rs[0] = G[n];
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void hermite_r_shared64(double* Rs, int st, const double* G, double X, double Y,
+                                                   double Z) {
+    Rs[0] = G[L];
+#pragma unroll 1
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll 1
+        for (int j = L - n; j >= 1; --j)
+#pragma unroll 1
+            for (int t = j; t >= 0; --t)
+#pragma unroll 1
+                for (int u = j - t; u >= 0; --u) {
+                    const int v = j - t - u;
+                    double r;
+                    if (t > 0) {
+                        r = X * Rs[hidx(t - 1, u, v) * st];
+                        if (t > 1) r += double(t - 1) * Rs[hidx(t - 2, u, v) * st];
+                    } else if (u > 0) {
+                        r = Y * Rs[hidx(t, u - 1, v) * st];
+                        if (u > 1) r += double(u - 1) * Rs[hidx(t, u - 2, v) * st];
+                    } else {
+                        r = Z * Rs[hidx(t, u, v - 1) * st];
+                        if (v > 1) r += double(v - 1) * Rs[hidx(t, u, v - 2) * st];
+                    }
+                    Rs[hidx(t, u, v) * st] = r;
+                }
+        Rs[0] = G[n];
+    }
+}
+
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(128) k_eri_big(EriArgs args) {
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+    constexpr int HAB = nherm(LAB), HCD = nherm(LCD), HL = nherm(L);
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    constexpr int SAB = PAIR32_STRIDE, SCD = PAIR32_STRIDE;
+    extern __shared__ float big_sh[];
+    const int st = blockDim.x;
+    float* const Rs = big_sh + threadIdx.x;                 // R:  [HL]
+    float* const Es_ab = Rs + HL * st;                     // E^ab: [3 * EAB]
+    float* const Es_cd = Es_ab + 3 * EAB * st;             // E^cd: [3 * ECD]
+    const float* __restrict__ bra = (const float*)args.bra;
+    const float* __restrict__ ket = (const float*)args.ket;
+    const float* __restrict__ boys = (const float*)args.boys;
+    const float* __restrict__ P = (const float*)args.P;
+    const int64_t i0 = args.range ? args.range[0] : args.i0, i1 = args.range ? args.range[1] : args.i1;
+    for (int64_t base = i0 + blockIdx.x * (int64_t)blockDim.x; base < i1; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const Quartet q = i < i1 ? args.rec[i] : Quartet{-1, -1};
+        const bool valid = q.ab >= 0 && q.ab < args.nab && q.cd >= 0 && q.cd < args.ncd;
+        int fa = -1, fc = -1, ldk = 0, ldp = 0;
+        double* Kb = args.K;
+        const float* Pb = P;
+        if (valid) {
+            const float* pb = bra + (int64_t)q.ab * SAB;
+            const float* pk = ket + (int64_t)q.cd * SCD;
+            const PairMeta mb = args.bmeta[q.ab], mk = args.kmeta[q.cd];
+            fa = mb.fa;
+            fc = mk.fa;
+            ldk = mb.ldk;
+            ldp = mb.ldp;
+            Kb = args.K + mb.krow_a + fc;
+            Pb = P + mb.prow_b + mk.fb;
+            // pair data, E tables into shared memory
+            const float4* b4 = reinterpret_cast<const float4*>(pb);
+            const float4* k4 = reinterpret_cast<const float4*>(pk);
+            float b[16], k[16];
+            sfor<4>([&](auto v_) {
+                constexpr int v = KX_CV(v_);
+                const float4 x = __ldg(b4 + v), y = __ldg(k4 + v);
+                b[4 * v] = x.x; b[4 * v + 1] = x.y; b[4 * v + 2] = x.z; b[4 * v + 3] = x.w;
+                k[4 * v] = y.x; k[4 * v + 1] = y.y; k[4 * v + 2] = y.z; k[4 * v + 3] = y.w;
+            });
+            const float X = (b[P32_PHI] - k[P32_PHI]) + (b[P32_PLO] - k[P32_PLO]);
+            const float Y = (b[P32_PHI + 1] - k[P32_PHI + 1]) + (b[P32_PLO + 1] - k[P32_PLO + 1]);
+            const float Z = (b[P32_PHI + 2] - k[P32_PHI + 2]) + (b[P32_PLO + 2] - k[P32_PLO + 2]);
+            sfor<3>([&](auto x_) {
+                constexpr int x = KX_CV(x_);
+                float e1[EAB];
+                e_build<LA, LB>(e1, b[P32_PA + x], b[P32_PB + x], b[P32_INV2P]);
+                sfor<EAB>([&](auto j_) { Es_ab[(x * EAB + KX_CV(j_)) * st] = e1[KX_CV(j_)]; });
+                float e2[ECD];
+                e_build<LC, LD>(e2, k[P32_PA + x], k[P32_PB + x], k[P32_INV2P]);
+                sfor<ECD>([&](auto j_) { Es_cd[(x * ECD + KX_CV(j_)) * st] = e2[KX_CV(j_)]; });
+            });
+            const float p = b[P32_P], qq = k[P32_P];
+            const float pq = p * qq, sum = p + qq;
+            const float rho = pq / sum;
+            const float r2 = X * X + Y * Y + Z * Z;
+            const float pref = float(2.0 * 17.493418327624862) * b[P32_KAB] * k[P32_KAB] / (pq * sqrtf(sum));
+            float G[L + 1];
+            boys_scaled<L, float>(G, rho * r2, rho, r2, pref, boys);
+            hermite_r_shared<L>(Rs, st, G, X, Y, Z);
+        }
+#pragma unroll 1
+        for (int inu = 0; inu < NC; ++inu) {
+            float kacc[NA];
+            sfor<NA>([&](auto e_) { kacc[KX_CV(e_)] = 0.f; });
+            if (valid) {
+                const int nx = cart_x(LC, inu), ny = cart_y(LC, inu), nz = cart_z(LC, inu);
+                // E^cd_{nu sig, h'} factors of this nu: per dimension
+                // E[n][s][t'] for s = 0..LD, t' = 0..LCD
+                float exd[LD + 1][LCD + 1], eyd[LD + 1][LCD + 1], ezd[LD + 1][LCD + 1];
+                sfor<LD + 1>([&](auto s_) {
+                    constexpr int s = KX_CV(s_);
+                    sfor<LCD + 1>([&](auto t_) {
+                        constexpr int t = KX_CV(t_);
+                        exd[s][t] = Es_cd[(0 * ECD + eidx(LC, LD, 0, s, t) + nx * (LD + 1) * (LCD + 1)) * st];
+                        eyd[s][t] = Es_cd[(1 * ECD + eidx(LC, LD, 0, s, t) + ny * (LD + 1) * (LCD + 1)) * st];
+                        ezd[s][t] = Es_cd[(2 * ECD + eidx(LC, LD, 0, s, t) + nz * (LD + 1) * (LCD + 1)) * st];
+                    });
+                });
+#pragma unroll 1
+                for (int ilam = 0; ilam < NB; ++ilam) {
+                    const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
+                    // T_{h'} = sum_sig E^cd_{nu sig,h'} P_{lam sig}
+                    float pv[ND];
+                    sfor<ND>([&](auto g_) { pv[KX_CV(g_)] = __ldg(Pb + ilam * ldp + KX_CV(g_)); });
+                    float T[HCD];
+                    sfor<HCD>([&](auto h_) { T[KX_CV(h_)] = 0.f; });
+                    sfor<ND>([&](auto g_) {
+                        constexpr int g = KX_CV(g_);
+                        constexpr int sx = cart_x(LD, g), sy = cart_y(LD, g), sz = cart_z(LD, g);
+                        sfor<LCD + 1>([&](auto t_) {
+                            constexpr int t = KX_CV(t_);
+                            const float a1 = pv[g] * exd[sx][t];
+                            sfor<LCD + 1 - t>([&](auto u_) {
+                                constexpr int u = KX_CV(u_);
+                                const float a2 = a1 * eyd[sy][u];
+                                sfor<LCD + 1 - t - u>([&](auto v_) {
+                                    constexpr int v = KX_CV(v_);
+                                    T[hidx(t, u, v)] += a2 * ezd[sz][v];
+                                });
+                            });
+                        });
+                    });
+                    // U_h = sum_{h'} (-1)^{|h'|} R_{h+h'} T_{h'}, R read once per s = h + h'
+                    float U[HAB];
+                    sfor<HAB>([&](auto h_) { U[KX_CV(h_)] = 0.f; });
+                    sfor<L + 1>([&](auto ts_) {
+                        constexpr int ts = KX_CV(ts_);
+                        sfor<L + 1 - ts>([&](auto us_) {
+                            constexpr int us = KX_CV(us_);
+                            sfor<L + 1 - ts - us>([&](auto vs_) {
+                                constexpr int vs = KX_CV(vs_);
+                                const float r = Rs[hidx(ts, us, vs) * st];
+                                sfor<(ts < LAB ? ts : LAB) + 1>([&](auto t_) {
+                                    constexpr int t = KX_CV(t_);
+                                    sfor<(us < LAB - t ? us : LAB - t) + 1>([&](auto u_) {
+                                        constexpr int u = KX_CV(u_);
+                                        sfor<(vs < LAB - t - u ? vs : LAB - t - u) + 1>([&](auto v_) {
+                                            constexpr int v = KX_CV(v_);
+                                            constexpr int t2 = ts - t, u2 = us - u, v2 = vs - v;
+                                            if constexpr (t2 + u2 + v2 <= LCD) {
+                                                if constexpr ((t2 + u2 + v2) & 1)
+                                                    U[hidx(t, u, v)] -= r * T[hidx(t2, u2, v2)];
+                                                else
+                                                    U[hidx(t, u, v)] += r * T[hidx(t2, u2, v2)];
+                                            }
+                                        });
+                                    });
+                                });
+                            });
+                        });
+                    });
+                    // K_{mu nu} += sum_h E^ab_{mu lam,h} U_h, E^ab factors of this lam
+                    float exa[LA + 1][LAB + 1], eya[LA + 1][LAB + 1], eza[LA + 1][LAB + 1];
+                    sfor<LA + 1>([&](auto m_) {
+                        constexpr int m = KX_CV(m_);
+                        sfor<LAB + 1>([&](auto t_) {
+                            constexpr int t = KX_CV(t_);
+                            exa[m][t] = Es_ab[(0 * EAB + eidx(LA, LB, m, 0, t) + lx * (LAB + 1)) * st];
+                            eya[m][t] = Es_ab[(1 * EAB + eidx(LA, LB, m, 0, t) + ly * (LAB + 1)) * st];
+                            eza[m][t] = Es_ab[(2 * EAB + eidx(LA, LB, m, 0, t) + lz * (LAB + 1)) * st];
+                        });
+                    });
+                    sfor<NA>([&](auto mu_) {
+                        constexpr int mu = KX_CV(mu_);
+                        constexpr int mx = cart_x(LA, mu), my = cart_y(LA, mu), mz = cart_z(LA, mu);
+                        float sacc = 0.f;
+                        sfor<LAB + 1>([&](auto t_) {
+                            constexpr int t = KX_CV(t_);
+                            sfor<LAB + 1 - t>([&](auto u_) {
+                                constexpr int u = KX_CV(u_);
+                                const float exy = exa[mx][t] * eya[my][u];
+                                float sz_ = 0.f;
+                                sfor<LAB + 1 - t - u>([&](auto v_) {
+                                    constexpr int v = KX_CV(v_);
+                                    sz_ += eza[mz][v] * U[hidx(t, u, v)];
+                                });
+                                sacc += exy * sz_;
+                            });
+                        });
+                        kacc[mu] += sacc;
+                    });
+                }
+            }
+            // column nu of the K block: warp-segmented sums over equal (fa, fc)
+            flush_k<NA, 1, float>(kacc, fa, fc, Kb + inu, ldk);
+        }
+    }
+}
+
+// FP64 variant for the largest classes: the same full-set (nu, lam) loop with
+// T and U in registers and R in the thread's slice of shared memory
+// (nherm(L) doubles, interleaved across the block); the E slices of each nu
+// and lam are read from the FP64 pair record itself (L1-resident while the
+// quartet is evaluated).  An alternative to the rolled kernel that the
+// autotuner may pick per class.
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(128) k_eri_big64(EriArgs args) {
+    using R = double;
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+    constexpr int HAB = nherm(LAB), HCD = nherm(LCD);
+    constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
+    constexpr int SAB = pair_stride(LA, LB), SCD = pair_stride(LC, LD);
+    extern __shared__ double big_sh64[];
+    const int st = blockDim.x;
+    double* const Rs = big_sh64 + threadIdx.x;
+    const R* __restrict__ bra = (const R*)args.bra;
+    const R* __restrict__ ket = (const R*)args.ket;
+    const R* __restrict__ boys = (const R*)args.boys;
+    const R* __restrict__ P = (const R*)args.P;
+    const int64_t i0 = args.range ? args.range[0] : args.i0, i1 = args.range ? args.range[1] : args.i1;
+    for (int64_t base = i0 + blockIdx.x * (int64_t)blockDim.x; base < i1; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const Quartet q = i < i1 ? args.rec[i] : Quartet{-1, -1};
+        const bool valid = q.ab >= 0 && q.ab < args.nab && q.cd >= 0 && q.cd < args.ncd;
+        int fa = -1, fc = -1, ldk = 0, ldp = 0;
+        double* Kb = args.K;
+        const R* Pb = P;
+        const R* Eab = bra;   // E tables of the two pair records (x, y, z blocks)
+        const R* Ecd = ket;
+        if (valid) {
+            const R* pb = bra + (int64_t)q.ab * SAB;
+            const R* pk = ket + (int64_t)q.cd * SCD;
+            const PairMeta mb = args.bmeta[q.ab], mk = args.kmeta[q.cd];
+            fa = mb.fa;
+            fc = mk.fa;
+            ldk = mb.ldk;
+            ldp = mb.ldp;
+            Kb = args.K + mb.krow_a + fc;
+            Pb = P + mb.prow_b + mk.fb;
+            Eab = pb + 5;
+            Ecd = pk + 5;
+            const R p = __ldg(pb), qq = __ldg(pk);
+            const R X = __ldg(pb + 1) - __ldg(pk + 1), Y = __ldg(pb + 2) - __ldg(pk + 2),
+                    Z = __ldg(pb + 3) - __ldg(pk + 3);
+            const R pq = p * qq, sum = p + qq;
+            const R rho = pq / sum;
+            const R r2 = X * X + Y * Y + Z * Z;
+            const R pref = R(2.0 * 17.493418327624862) * __ldg(pb + 4) * __ldg(pk + 4) / (pq * sqrt(sum));
+            R G[L + 1];
+            boys_scaled<L, R>(G, rho * r2, rho, r2, pref, boys);
+            hermite_r_shared64<L>(Rs, st, G, X, Y, Z);
+        }
+#pragma unroll 1
+        for (int inu = 0; inu < NC; ++inu) {
+            R kacc[NA];
+            sfor<NA>([&](auto e_) { kacc[KX_CV(e_)] = R(0); });
+            if (valid) {
+                const int nx = cart_x(LC, inu), ny = cart_y(LC, inu), nz = cart_z(LC, inu);
+#pragma unroll 1
+                for (int ilam = 0; ilam < NB; ++ilam) {
+                    const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
+                    R T[HCD];
+                    {
+                        R exd[LD + 1][LCD + 1], eyd[LD + 1][LCD + 1], ezd[LD + 1][LCD + 1];
+                        sfor<LD + 1>([&](auto s_) {
+                            constexpr int s = KX_CV(s_);
+                            sfor<LCD + 1>([&](auto t_) {
+                                constexpr int t = KX_CV(t_);
+                                exd[s][t] = __ldg(Ecd + 0 * ECD + eidx(LC, LD, 0, s, t) + nx * (LD + 1) * (LCD + 1));
+                                eyd[s][t] = __ldg(Ecd + 1 * ECD + eidx(LC, LD, 0, s, t) + ny * (LD + 1) * (LCD + 1));
+                                ezd[s][t] = __ldg(Ecd + 2 * ECD + eidx(LC, LD, 0, s, t) + nz * (LD + 1) * (LCD + 1));
+                            });
+                        });
+                        R pv[ND];
+                        sfor<ND>([&](auto g_) { pv[KX_CV(g_)] = __ldg(Pb + ilam * ldp + KX_CV(g_)); });
+                        sfor<HCD>([&](auto h_) { T[KX_CV(h_)] = R(0); });
+                        sfor<ND>([&](auto g_) {
+                            constexpr int g = KX_CV(g_);
+                            constexpr int sx = cart_x(LD, g), sy = cart_y(LD, g), sz = cart_z(LD, g);
+                            sfor<LCD + 1>([&](auto t_) {
+                                constexpr int t = KX_CV(t_);
+                                const R a1 = pv[g] * exd[sx][t];
+                                sfor<LCD + 1 - t>([&](auto u_) {
+                                    constexpr int u = KX_CV(u_);
+                                    const R a2 = a1 * eyd[sy][u];
+                                    sfor<LCD + 1 - t - u>([&](auto v_) {
+                                        constexpr int v = KX_CV(v_);
+                                        T[hidx(t, u, v)] += a2 * ezd[sz][v];
+                                    });
+                                });
+                            });
+                        });
+                    }
+                    R U[HAB];
+                    sfor<HAB>([&](auto h_) { U[KX_CV(h_)] = R(0); });
+                    sfor<L + 1>([&](auto ts_) {
+                        constexpr int ts = KX_CV(ts_);
+                        sfor<L + 1 - ts>([&](auto us_) {
+                            constexpr int us = KX_CV(us_);
+                            sfor<L + 1 - ts - us>([&](auto vs_) {
+                                constexpr int vs = KX_CV(vs_);
+                                const R r = Rs[hidx(ts, us, vs) * st];
+                                sfor<(ts < LAB ? ts : LAB) + 1>([&](auto t_) {
+                                    constexpr int t = KX_CV(t_);
+                                    sfor<(us < LAB - t ? us : LAB - t) + 1>([&](auto u_) {
+                                        constexpr int u = KX_CV(u_);
+                                        sfor<(vs < LAB - t - u ? vs : LAB - t - u) + 1>([&](auto v_) {
+                                            constexpr int v = KX_CV(v_);
+                                            constexpr int t2 = ts - t, u2 = us - u, v2 = vs - v;
+                                            if constexpr (t2 + u2 + v2 <= LCD) {
+                                                if constexpr ((t2 + u2 + v2) & 1)
+                                                    U[hidx(t, u, v)] -= r * T[hidx(t2, u2, v2)];
+                                                else
+                                                    U[hidx(t, u, v)] += r * T[hidx(t2, u2, v2)];
+                                            }
+                                        });
+                                    });
+                                });
+                            });
+                        });
+                    });
+                    R exa[LA + 1][LAB + 1], eya[LA + 1][LAB + 1], eza[LA + 1][LAB + 1];
+                    sfor<LA + 1>([&](auto m_) {
+                        constexpr int m = KX_CV(m_);
+                        sfor<LAB + 1>([&](auto t_) {
+                            constexpr int t = KX_CV(t_);
+                            exa[m][t] = __ldg(Eab + 0 * EAB + eidx(LA, LB, m, 0, t) + lx * (LAB + 1));
+                            eya[m][t] = __ldg(Eab + 1 * EAB + eidx(LA, LB, m, 0, t) + ly * (LAB + 1));
+                            eza[m][t] = __ldg(Eab + 2 * EAB + eidx(LA, LB, m, 0, t) + lz * (LAB + 1));
+                        });
+                    });
+                    sfor<NA>([&](auto mu_) {
+                        constexpr int mu = KX_CV(mu_);
+                        constexpr int mx = cart_x(LA, mu), my = cart_y(LA, mu), mz = cart_z(LA, mu);
+                        R sacc = R(0);
+                        sfor<LAB + 1>([&](auto t_) {
+                            constexpr int t = KX_CV(t_);
+                            sfor<LAB + 1 - t>([&](auto u_) {
+                                constexpr int u = KX_CV(u_);
+                                const R exy = exa[mx][t] * eya[my][u];
+                                R sz_ = R(0);
+                                sfor<LAB + 1 - t - u>([&](auto v_) {
+                                    constexpr int v = KX_CV(v_);
+                                    sz_ += eza[mz][v] * U[hidx(t, u, v)];
+                                });
+                                sacc += exy * sz_;
+                            });
+                        });
+                        kacc[mu] += sacc;
+                    });
+                }
+            }
+            flush_k<NA, 1, R>(kacc, fa, fc, Kb + inu, ldk);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // algorithmic FLOP count of one quartet (mirrors the loops above)
 // ---------------------------------------------------------------------------
 
@@ -899,25 +1314,32 @@ double eri_flops() {
     return f;
 }
 
-// The kernel of a class and precision (unrolled below ROLL_L, rolled above).
+// The kernel of a class and precision: unrolled below ROLL_L; above it the
+// rolled kernel in FP64 and the shared-memory kernel in FP32.
+// variant 1 (large classes only): the shared-memory kernel; FP32 uses it by
+// default, FP64 when the autotuner finds it faster than the rolled kernel
 template <int LA, int LB, int LC, int LD>
-EriKernel eri_kernel(int prec) {
-    if constexpr (LA + LB + LC + LD < ROLL_L)
-        return prec == 0 ? &k_eri<LA, LB, LC, LD, double> : &k_eri<LA, LB, LC, LD, float>;
-    else
-        return prec == 0 ? &k_eri_rolled<LA, LB, LC, LD, double> : &k_eri_rolled<LA, LB, LC, LD, float>;
+EriKern eri_kernel(int prec, int variant) {
+    if constexpr (LA + LB + LC + LD < ROLL_L) {
+        return {prec == 0 ? &k_eri<LA, LB, LC, LD, double> : &k_eri<LA, LB, LC, LD, float>, 0, 1};
+    } else {
+        if (prec == 1) return {&k_eri_big<LA, LB, LC, LD>, (int)sizeof(float) * big_slice<LA, LB, LC, LD>(), 1};
+        if (variant == 1)
+            return {&k_eri_big64<LA, LB, LC, LD>, (int)sizeof(double) * nherm(LA + LB + LC + LD), 2};
+        return {&k_eri_rolled<LA, LB, LC, LD, double>, 0, 2};
+    }
 }
 
 // dispatch over (lc, ld) for a fixed bra pair class (la, lb)
 #define KX_ERI_CASE(LA_, LB_, LC_, LD_) \
-    case LC_ * 3 + LD_: return eri_kernel<LA_, LB_, LC_, LD_>(prec);
+    case LC_ * 3 + LD_: return eri_kernel<LA_, LB_, LC_, LD_>(prec, variant);
 #define KX_ERI_DISPATCH(LA_, LB_)                                                                        \
-    EriKernel eri_kernel_ab##LA_##LB_(int cls, int prec) {                                               \
+    EriKern eri_kernel_ab##LA_##LB_(int cls, int prec, int variant) {                                    \
         switch (cls % 9) {                                                                               \
             KX_ERI_CASE(LA_, LB_, 0, 0) KX_ERI_CASE(LA_, LB_, 0, 1) KX_ERI_CASE(LA_, LB_, 0, 2)          \
             KX_ERI_CASE(LA_, LB_, 1, 0) KX_ERI_CASE(LA_, LB_, 1, 1) KX_ERI_CASE(LA_, LB_, 1, 2)          \
             KX_ERI_CASE(LA_, LB_, 2, 0) KX_ERI_CASE(LA_, LB_, 2, 1) KX_ERI_CASE(LA_, LB_, 2, 2)          \
-            default: return nullptr;                                                                     \
+            default: return EriKern{nullptr, 0, 0};                                                      \
         }                                                                                                \
     }                                                                                                    \
     double class_flops_ab##LA_##LB_(int cls) {                                                           \

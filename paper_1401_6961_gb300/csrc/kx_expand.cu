@@ -345,19 +345,35 @@ int expand_write_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* 
 // class dispatch
 // ---------------------------------------------------------------------------
 
-EriKernel eri_kernel(int cls, int prec) {
+EriKern eri_kernel(int cls, int prec, int variant) {
     switch (cls / 9) {
-        case 0: return eri_kernel_ab00(cls, prec);
-        case 1: return eri_kernel_ab01(cls, prec);
-        case 2: return eri_kernel_ab02(cls, prec);
-        case 3: return eri_kernel_ab10(cls, prec);
-        case 4: return eri_kernel_ab11(cls, prec);
-        case 5: return eri_kernel_ab12(cls, prec);
-        case 6: return eri_kernel_ab20(cls, prec);
-        case 7: return eri_kernel_ab21(cls, prec);
-        case 8: return eri_kernel_ab22(cls, prec);
-        default: return nullptr;
+        case 0: return eri_kernel_ab00(cls, prec, variant);
+        case 1: return eri_kernel_ab01(cls, prec, variant);
+        case 2: return eri_kernel_ab02(cls, prec, variant);
+        case 3: return eri_kernel_ab10(cls, prec, variant);
+        case 4: return eri_kernel_ab11(cls, prec, variant);
+        case 5: return eri_kernel_ab12(cls, prec, variant);
+        case 6: return eri_kernel_ab20(cls, prec, variant);
+        case 7: return eri_kernel_ab21(cls, prec, variant);
+        case 8: return eri_kernel_ab22(cls, prec, variant);
+        default: return EriKern{nullptr, 0, 0};
     }
+}
+
+constexpr int SMEM_BLOCK_MAX = 227 * 1024;   // opt-in shared memory per block
+
+int eri_fit_threads(const EriKern& k, int threads) {
+    while (k.smem_per_thread > 0 && threads > 32 && threads * k.smem_per_thread > SMEM_BLOCK_MAX) threads /= 2;
+    return threads;
+}
+
+int eri_prepare(kx_ctx* c, int s, int variant, const EriKern& k) {
+    if (k.smem_per_thread > 0 && !c->eri_smem_set[s][variant & 1]) {
+        KX_CUDA(c, cudaFuncSetAttribute((const void*)k.k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM_BLOCK_MAX));
+        c->eri_smem_set[s][variant & 1] = true;
+    }
+    return KX_OK;
 }
 
 EriArgs eri_args(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1, const int64_t* range,
@@ -383,10 +399,12 @@ EriArgs eri_args(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, i
 int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1, const int64_t* range,
                const double* P, double* K) {
     if (!range && i1 <= i0) return KX_OK;
-    EriKernel k = eri_kernel(cls, prec);
-    if (!k) return set_err(c, KX_EINVAL, "bad class");
     const int s = prec * NCLASS + cls;
-    const int threads = c->eri_threads[s];
+    const EriKern kk = eri_kernel(cls, prec, c->eri_variant[s]);
+    if (!kk.k) return set_err(c, KX_EINVAL, "bad class");
+    KX_TRY(eri_prepare(c, s, c->eri_variant[s], kk));
+    const int threads = eri_fit_threads(kk, c->eri_threads[s]);
+    const size_t smem = (size_t)threads * kk.smem_per_thread;
     int64_t blocks;
     if (range) {
         // device-side range (captured launches): always a persistent grid
@@ -396,7 +414,7 @@ int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int
         if (c->eri_bpsm[s] > 0) blocks = std::min<int64_t>(blocks, (int64_t)c->eri_bpsm[s] * c->n_sm);
     }
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)1 << 30));
-    k<<<(unsigned)blocks, threads, 0, c->stream>>>(eri_args(c, cls, prec, rec, i0, i1, range, P, K));
+    kk.k<<<(unsigned)blocks, threads, smem, c->stream>>>(eri_args(c, cls, prec, rec, i0, i1, range, P, K));
     return KX_OK;
 }
 

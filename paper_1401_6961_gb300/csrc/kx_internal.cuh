@@ -267,6 +267,8 @@ struct kx_ctx {
     // persistent blocks per SM (0 = one thread per record); see kx_autotune
     int eri_threads[2 * kx::NCLASS] = {};
     int eri_bpsm[2 * kx::NCLASS] = {};
+    int eri_variant[2 * kx::NCLASS] = {};       // kernel variant of the stream
+    bool eri_smem_set[2 * kx::NCLASS][2] = {};  // dynamic shared memory limit raised, per variant
     int n_sm = 0;
     bool tuned[2 * kx::NCLASS] = {};
     // what the last eager build saw (sizes for a captured plan)
@@ -404,17 +406,23 @@ struct EriArgs {
     int64_t nab, ncd;
 };
 typedef void (*EriKernel)(EriArgs);
+// a class kernel and the dynamic shared memory it needs per thread of a block
+struct EriKern {
+    EriKernel k;
+    int smem_per_thread;
+    int n_variants;       // kernels available for this stream (see eri_kernel)
+};
 
-EriKernel eri_kernel(int cls, int prec);          // kx_expand.cu, over the nine below
-EriKernel eri_kernel_ab00(int cls, int prec);
-EriKernel eri_kernel_ab01(int cls, int prec);
-EriKernel eri_kernel_ab02(int cls, int prec);
-EriKernel eri_kernel_ab10(int cls, int prec);
-EriKernel eri_kernel_ab11(int cls, int prec);
-EriKernel eri_kernel_ab12(int cls, int prec);
-EriKernel eri_kernel_ab20(int cls, int prec);
-EriKernel eri_kernel_ab21(int cls, int prec);
-EriKernel eri_kernel_ab22(int cls, int prec);
+EriKern eri_kernel(int cls, int prec, int variant);   // kx_expand.cu, over the nine below
+EriKern eri_kernel_ab00(int cls, int prec, int variant);
+EriKern eri_kernel_ab01(int cls, int prec, int variant);
+EriKern eri_kernel_ab02(int cls, int prec, int variant);
+EriKern eri_kernel_ab10(int cls, int prec, int variant);
+EriKern eri_kernel_ab11(int cls, int prec, int variant);
+EriKern eri_kernel_ab12(int cls, int prec, int variant);
+EriKern eri_kernel_ab20(int cls, int prec, int variant);
+EriKern eri_kernel_ab21(int cls, int prec, int variant);
+EriKern eri_kernel_ab22(int cls, int prec, int variant);
 double class_flops_ab00(int cls);
 double class_flops_ab01(int cls);
 double class_flops_ab02(int cls);
@@ -431,6 +439,11 @@ EriArgs eri_args(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, i
 // shape for that stream
 int eri_launch(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, int64_t i1, const int64_t* range,
                const double* P, double* K);
+// threads per block a stream's kernel can use (its shared memory bounds it),
+// and the dynamic shared memory of a launch of that many threads; raises the
+// kernel's shared-memory limit once per context
+int eri_fit_threads(const EriKern& k, int threads);
+int eri_prepare(kx_ctx* c, int s, int variant, const EriKern& k);
 
 // algorithmic FLOPs of one shell quartet of a class (the counter of the ERI kernels)
 double class_flops(int cls);

@@ -338,27 +338,34 @@ int process_leaves(Run& r, const Task* leaves, int64_t n);
 int finish_run(kx_ctx* c, kx_stats* st, Timer& tm, int D);
 
 // Launch-shape autotuner of one (precision, class) stream: times every
-// candidate shape on (a prefix of) the stream's records, accumulating into a
-// scratch K, and keeps the fastest.  Candidates: 64, 128 and 256 threads per
-// block, each with one thread per record or a persistent grid of 1x or 2x
-// the blocks that fit on an SM.
+// candidate on (a prefix of) the stream's records, accumulating into a
+// scratch K, and keeps the fastest.  Candidates: each kernel variant of the
+// stream (the FP64 large classes have two), with 64, 128 and 256 threads per
+// block (as far as its shared memory allows), each with one thread per
+// record or a persistent grid of 1x or 2x the blocks that fit on an SM.
 constexpr int64_t TUNE_MIN = 1 << 14;      // records needed to tune a stream
 constexpr int64_t TUNE_MAX = 1 << 19;      // records timed per candidate
 int tune_stream(kx_ctx* c, int s, const Quartet* rec, int64_t i0, int64_t i1, const double* P) {
     if (i1 - i0 < TUNE_MIN) return KX_OK;
     const int prec = s / NCLASS, cls = s % NCLASS;
-    EriKernel k = eri_kernel(cls, prec);
-    if (!k) return set_err(c, KX_EINVAL, "bad class");
+    const int nvar = eri_kernel(cls, prec, 0).n_variants;
     const int64_t j1 = std::min(i1, i0 + TUNE_MAX);
     const EriArgs args = eri_args(c, cls, prec, rec, i0, j1, nullptr, P, c->d_tuneK);
     cudaEvent_t e0, e1;
     KX_CUDA(c, cudaEventCreate(&e0));
     KX_CUDA(c, cudaEventCreate(&e1));
     float best = 1e30f;
-    int bt = ERI_THREADS, bb = 0;
+    int bt = ERI_THREADS, bb = 0, bv = 0;
+    for (int variant = 0; variant < nvar; ++variant) {
+    const EriKern kk = eri_kernel(cls, prec, variant);
+    if (!kk.k) return set_err(c, KX_EINVAL, "bad class");
+    KX_TRY(eri_prepare(c, s, variant, kk));
+    EriKernel k = kk.k;
     for (int threads : {64, 128, 256}) {
+        if (eri_fit_threads(kk, threads) != threads) continue;
+        const size_t smem = (size_t)threads * kk.smem_per_thread;
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0) != cudaSuccess || occ < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem) != cudaSuccess || occ < 1) {
             (void)cudaGetLastError();
             continue;
         }
@@ -368,7 +375,7 @@ int tune_stream(kx_ctx* c, int s, const Quartet* rec, int64_t i0, int64_t i1, co
             float t = 0.f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, c->stream);
-                k<<<(unsigned)blocks, threads, 0, c->stream>>>(args);
+                k<<<(unsigned)blocks, threads, smem, c->stream>>>(args);
                 cudaEventRecord(e1, c->stream);
                 KX_CUDA(c, cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -379,14 +386,17 @@ int tune_stream(kx_ctx* c, int s, const Quartet* rec, int64_t i0, int64_t i1, co
                 best = t;
                 bt = threads;
                 bb = bpsm;
+                bv = variant;
             }
         }
+    }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     KX_CUDA(c, cudaGetLastError());
     c->eri_threads[s] = bt;
     c->eri_bpsm[s] = bb;
+    c->eri_variant[s] = bv;
     c->tuned[s] = true;
     return KX_OK;
 }

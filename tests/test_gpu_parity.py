@@ -145,6 +145,38 @@ def test_random_shells_all_classes(kx, seed):
         assert np.abs(K - K0).max() <= TOL64 * max(1.0, np.abs(K0).max())
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_shells_all_classes_fp32(kx, seed):
+    """Every class through its FP32 kernel (split above every bound): the
+    error is FP32 rounding of the integrals, bounded relative to max|K|."""
+    sys_ = wl.random_shells(9, seed, lmax=2, box=2.5)
+    P = wl.density(sys_, 100 + seed)
+    K0 = oracle.exchange_direct(sys_, P)
+    K, ex = _gpu_k(kx, sys_, P, leaf_max=6, tau=0.0, precision=kx.KX_MIXED, split_threshold=1e30)
+    assert ex.stats.n_shell_quartets_fp64 == 0
+    assert np.abs(K - K0).max() <= 2e-5 * np.abs(K0).max()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_shells_fp64_shared_memory_variant(kx, seed):
+    """The FP64 large classes through their second kernel (shared-memory R,
+    full Hermite sets), forced for every such class."""
+    sys_ = wl.random_shells(9, seed, lmax=2, box=2.5)
+    P = wl.density(sys_, 100 + seed)
+    K0 = oracle.exchange_direct(sys_, P)
+    import torch
+    ex = kx.Exchange(sys_, leaf_max=6)
+    big = [c for c in range(81) if c // 27 + c // 9 % 3 + c // 3 % 3 + c % 3 >= 7]
+    for c in big:
+        kx.kx_set_launch_shape(ex.ctx, c, 128, 0, 1)
+    assert kx.kx_get_launch_shapes(ex.ctx)[2][big].tolist() == [1] * len(big)
+    with pytest.raises(kx.KxError):
+        kx.kx_set_launch_shape(ex.ctx, 0, 128, 0, 1)      # (ss|ss) has one kernel
+    K = ex(torch.from_numpy(P).cuda(), tau=0.0).cpu().numpy()
+    assert np.abs(K - K0).max() <= TOL64 * max(1.0, np.abs(K0).max())
+    ex.close()
+
+
 def test_medium_basis_three_waters(kx):
     big = wl.water64(2)
     s = wl.build_system("w3", big.symbols[:9], big.xyz[:9] / wl.BOHR_PER_ANGSTROM, "medium")
