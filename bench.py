@@ -548,7 +548,8 @@ def run_ours(args):
             "launch": "one captured CUDA graph per build (kx_graph_plan / kx_graph_launch), autotuned "
                       f"class-kernel shapes ({n_tuned} streams tuned)",
             "eager": {"value": ws * 1e3 / ms_e, "unit": UNIT, "ms_per_step": ms_e,
-                      "steps": max(1, args.eager_steps), "profile": "CUDA events around every class launch"},
+                      "steps": max(1, args.eager_steps), "launches_per_step": int(ste.n_launches),
+                      "profile": "CUDA events around every class launch"},
             "stages_ms_eager": {"norms": ste.ms_norms, "traverse": ste.ms_traverse, "expand": ste.ms_expand,
                                 "eri": ste.ms_eri},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
