@@ -106,6 +106,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_name(kx, ctx, s: int) -> str:
+    """Name of the kernel that runs stream s (precision * 81 + class)."""
+    cls = s % 81
+    la, lb, lc, ld = cls // 27, (cls // 9) % 3, (cls // 3) % 3, cls % 3
+    args = f"{la},{lb},{lc},{ld}"
+    if la + lb + lc + ld < 7:
+        return f"k_eri<{args},{'double' if s < 81 else 'float'}>"
+    if s >= 81:
+        return f"k_eri_big<{args}>"
+    variant = int(kx.kx_get_launch_shapes(ctx)[2][s])
+    return f"k_eri_big64<{args}>" if variant == 1 else f"k_eri_rolled<{args},double>"
+
+
 def barrier(ws: int) -> None:
     """All ranks meet (no-op for one rank)."""
     if ws > 1:
@@ -369,7 +382,7 @@ def run_batch(args):
                                 "eri": ste.ms_eri, "total": ste.ms_total},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": f"k_eri<{la},{lb},{lc},{ld},{'double' if prec_dom == 'fp64' else 'float'}>",
+                         "kernel": kernel_name(kx, bx.ctx, s_dom),
                          "measured": "CUDA events around each launch of that kernel in an eager profiled build "
                                      "of the same batch (a graph replay cannot be split by events)",
                          "peak_source": f"measured FMA probe ({prec_dom} pipe), kx_peak_probe"},
@@ -554,7 +567,7 @@ def run_ours(args):
                                 "eri": ste.ms_eri},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": f"k_eri<{la},{lb},{lc},{ld},{'double' if prec_dom == 'fp64' else 'float'}>",
+                         "kernel": kernel_name(kx, ex.ctx, s_dom),
                          "launches": int(prof["launches"][s_dom]),
                          "ms_per_launch": dom_ms / dom_launch,
                          "measured": "CUDA events on the launching stream around each launch of that kernel, "
