@@ -239,12 +239,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(sys_, precision, name, symmetric=True):
+def workload_config(sys_, precision, name, symmetric=True, leaf_max=10):
     nw = sys_.n_atom // 3
     return {"workload": f"(H2O){nw} water cluster at 1 g/cm^3, even-tempered medium basis "
                         f"({sys_.n_fn} functions, {sys_.n_shell} shells), tau=1e-10",
             "name": name,
-            "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": 10,
+            "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": leaf_max,
             "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
             "shell_screen": True, "symmetric": bool(symmetric),
             "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB buffer written)",
@@ -418,7 +418,7 @@ def run_ours(args):
     kx.load()
     sys_, P = wl.workload(args.workload)
     stream = torch.cuda.current_stream(dev)
-    ex = kx.Exchange(sys_, device=local, stream=stream)
+    ex = kx.Exchange(sys_, device=local, stream=stream, leaf_max=args.leaf_max)
     n = sys_.n_fn
     Pd = torch.from_numpy(P).to(dev)
     Kd = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -502,6 +502,19 @@ def run_ours(args):
     peak32 = kx.kx_peak_probe(local, kx.KX_MIXED) / 1e3
     peak = peak64 if prec_dom == "fp64" else peak32
     eri_ms = float(prof["ms"].sum())
+    # the ten costliest class streams of the eager builds
+    top = []
+    for s_ in np.argsort(-prof["ms"])[:10]:
+        s_ = int(s_)
+        if prof["ms"][s_] <= 0:
+            break
+        c_ = s_ % 81
+        top.append({"class": "({}{}|{}{})".format(*("spd"[x] for x in (c_ // 27, (c_ // 9) % 3, (c_ // 3) % 3,
+                                                                       c_ % 3))),
+                    "precision": "fp64" if s_ < 81 else "fp32", "kernel": kernel_name(kx, ex.ctx, s_),
+                    "ms": float(prof["ms"][s_]) / max(1, args.eager_steps),
+                    "quartets": int(prof["n"][s_]) // max(1, args.eager_steps),
+                    "tflops": float(prof["flops"][s_] / (prof["ms"][s_] * 1e-3) / 1e12)})
     eri_flops64 = float(prof["flops"][:81].sum())
     eri_flops32 = float(prof["flops"][81:].sum())
 
@@ -554,7 +567,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": workload_config(sys_, "mixed", args.workload, sym),
+            "config": workload_config(sys_, "mixed", args.workload, sym, args.leaf_max),
             "quartets_per_s": ws * quartets / (ms_step * 1e-3),
             "shell_quartets": quartets, "leaf_quartets": st.n_leaf_quartets,
             "shell_quartets_fp64": st.n_shell_quartets_fp64,
@@ -573,10 +586,11 @@ def run_ours(args):
                          "measured": "CUDA events on the launching stream around each launch of that kernel, "
                                      "in the eager builds of the same system that follow the timed replays",
                          "peak_source": f"measured FMA probe ({prec_dom} pipe), kx_peak_probe"},
-            "eri_stage": {"ms_per_step": eri_ms / args.steps,
+            "eri_classes_top": top,
+            "eri_stage": {"ms_per_step": eri_ms / max(1, args.eager_steps),
                           "tflops": (eri_flops64 + eri_flops32) / (eri_ms * 1e-3) / 1e12,
-                          "flops_fp64_per_step": eri_flops64 / args.steps,
-                          "flops_fp32_per_step": eri_flops32 / args.steps,
+                          "flops_fp64_per_step": eri_flops64 / max(1, args.eager_steps),
+                          "flops_fp32_per_step": eri_flops32 / max(1, args.eager_steps),
                           "peak_fp64_tflops": peak64, "peak_fp32_tflops": peak32},
             "fp64_plain": fp64,
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
@@ -591,6 +605,190 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+
+# ---------------------------------------------------------------------------
+# studies (not the benchmark line): the scaling sweep and the learned culling
+# ---------------------------------------------------------------------------
+
+SWEEP_N = (64, 128, 256, 512)
+SWEEP_TAU = (1e-10, 1e-8, 1e-6)
+SWEEP_BUILD_S = 25.0      # time a build only when the count predicts at most this many seconds
+SWEEP_MAX_SHELL_Q = 2e12  # counts (traversal + count pass of the screen) stay within about 20 s
+SWEEP_MAX_LEAF_Q = 1e10   # and the frontier before the last level within a few tens of GB
+RATE_MIXED, RATE_FP64 = 6e9, 1e9   # shell quartets/s of the (H2O)64 builds, for that prediction
+
+
+def _event_ms(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_sweep(args):
+    """Scaling sweep (H2O)_n, n = 64..512 at 1 g/cm^3, tau in {1e-10, 1e-8,
+    1e-6}: survivors of the plain method (every K block) against n, their
+    growth exponent next to the N lg N trend, and timed mixed / FP64 builds
+    (symmetric) where they fit the time cap."""
+    import numpy as np
+    import torch
+
+    import paper_1401_6961_gb300 as kx
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    kx.load()
+    stream = torch.cuda.current_stream(dev)
+    bases = [b.strip() for b in args.sweep_bases.split(",") if b.strip()]
+    ns = [int(x) for x in args.sweep_n.split(",")]
+    rows = []
+    last = {}
+    for basis in bases:
+        for nw in ns:
+            sys_ = wl.water_sweep(nw, basis)
+            taus = []
+            for tau in SWEEP_TAU:
+                prev = last.get((basis, tau))
+                if prev is not None:
+                    # cubic growth from the previous size: a generous prediction
+                    g = (sys_.n_fn / prev[0]) ** 3
+                    if prev[1] * g > SWEEP_MAX_SHELL_Q or prev[2] * g > SWEEP_MAX_LEAF_Q:
+                        rows.append({"basis": basis, "n_water": nw, "n_fn": sys_.n_fn, "tau": tau,
+                                     "skipped": f"predicted more than {SWEEP_MAX_SHELL_Q:.0e} shell quartets or "
+                                                f"{SWEEP_MAX_LEAF_Q:.0e} leaf quartets"})
+                        continue
+                taus.append(tau)
+            if not taus:
+                continue
+            P = wl.density(sys_, 5000 + nw)
+            t0 = time.perf_counter()
+            ex = kx.Exchange(sys_, device=0, stream=stream)
+            setup_s = time.perf_counter() - t0
+            Pd = torch.from_numpy(P).to(dev)
+            del P
+            K = torch.empty_like(Pd)
+            for tau in taus:
+                mixed = dict(tau=tau, precision=kx.KX_MIXED, split_threshold=SPLIT)
+                ms_c, full = _event_ms(stream, lambda: ex.count(Pd, symmetric=0, **mixed))
+                last[(basis, tau)] = (sys_.n_fn, full.n_shell_quartets, full.n_leaf_quartets)
+                half = ex.count(Pd, symmetric=1, **mixed)
+                row = {"basis": basis, "n_water": nw, "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": tau,
+                       "leaf_quartets": full.n_leaf_quartets, "shell_quartets": full.n_shell_quartets,
+                       "candidates": full.n_candidates, "shell_quartets_symmetric": half.n_shell_quartets,
+                       "shell_quartets_fp64_symmetric": half.n_shell_quartets_fp64,
+                       "count_ms": ms_c, "setup_s": setup_s}
+                q = half.n_shell_quartets
+                if q / RATE_MIXED <= SWEEP_BUILD_S:
+                    ex(Pd, out=K, symmetric=1, **mixed)            # warm-up
+                    ms, _ = _event_ms(stream, lambda: ex(Pd, out=K, symmetric=1, **mixed))
+                    row["mixed_ms"] = ms
+                    row["mixed_quartets_per_s"] = q / (ms * 1e-3)
+                    if q / RATE_FP64 <= SWEEP_BUILD_S:
+                        Km = K.clone()
+                        ms64, _ = _event_ms(stream, lambda: ex(Pd, out=K, symmetric=1, tau=tau,
+                                                               precision=kx.KX_FP64))
+                        row["fp64_ms"] = ms64
+                        row["speedup_mixed_vs_fp64"] = ms64 / ms
+                        row["max_abs_dK_mixed_vs_fp64"] = float((Km - K).abs().max().item())
+                        del Km
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+            ex.close()
+            del Pd, K
+            torch.cuda.empty_cache()
+    # growth exponents: least squares of log(survivors) against log(n_fn)
+    fits = []
+    for basis in bases:
+        for tau in SWEEP_TAU:
+            pts = [(r["n_fn"], r["shell_quartets"], r["leaf_quartets"]) for r in rows
+                   if r["basis"] == basis and r["tau"] == tau and r.get("shell_quartets", 0) > 0]
+            if len(pts) < 2:
+                continue
+            x = np.log([p[0] for p in pts])
+            fits.append({"basis": basis, "tau": tau,
+                         "exponent_shell_quartets": float(np.polyfit(x, np.log([p[1] for p in pts]), 1)[0]),
+                         "exponent_leaf_quartets": float(np.polyfit(x, np.log([p[2] for p in pts]), 1)[0]),
+                         "exponent_n_lg_n": float(np.polyfit(x, np.log([p[0] * math.log2(p[0]) for p in pts]),
+                                                             1)[0])})
+    print(json.dumps({"study": "sweep", "workload": "(H2O)_n at 1 g/cm^3, n = " + ",".join(map(str, ns)),
+                      "split_threshold": SPLIT, "leaf_max": 10, "points": rows, "fits": fits}), flush=True)
+
+
+def run_learned(args):
+    """Learned culling: train the network on traces of small water clusters,
+    two clusters of the batched workload and a short alkane, then compare on
+    alkanes C_nH_2n+2 and (H2O)_256 (small basis, tau = 1e-8) the plain FP64
+    build, the plain mixed build and the mixed build with learned culling."""
+    import torch
+
+    import paper_1401_6961_gb300 as kx
+    import workloads as wl
+    from paper_1401_6961_gb300 import learned
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    kx.load()
+    stream = torch.cuda.current_stream(dev)
+    tau = 1e-8
+    w8, c6 = wl.water_cluster(8, 8, "small"), wl.alkane(6, 66, "small")
+    train_sets = [("water4", *wl.workload("water4")), ("(H2O)8", w8, wl.density(w8, 808)),
+                  ("C6H14", c6, wl.density(c6, 812))]
+    batch_sys, batch_dens = wl.batch_workload()
+    for i in (0, 1):
+        train_sets.append((f"batch cluster {i} ({batch_sys[i].n_atom // 3} waters)", batch_sys[i], batch_dens[i]))
+    tr = None
+    t0 = time.perf_counter()
+    for name, s, P in train_sets:
+        ex = kx.Exchange(s, device=0, stream=stream)
+        t = learned.traces(ex, torch.from_numpy(P).to(dev), tau, max_samples=20000, seed=1)
+        tr = t if tr is None else tr + t
+        ex.close()
+    t_tr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model = learned.train(tr, epochs=args.epochs, lr=3e-3, batch=4096)
+    t_train = time.perf_counter() - t0
+    evals = []
+    targets = [(f"C{n}H{2 * n + 2}", wl.alkane(n, 6000 + n), 7000 + n) for n in (10, 20, 40, 80)]
+    s256 = wl.water_sweep(256, "small")
+    targets.append(("(H2O)256", s256, 5256))
+    for name, s, pseed in targets:
+        Pd = torch.from_numpy(wl.density(s, pseed)).to(dev)
+        ex = kx.Exchange(s, device=0, stream=stream)
+        K64 = torch.empty_like(Pd)
+        ex(Pd, out=K64, tau=tau)                                            # warm-up
+        ms64, _ = _event_ms(stream, lambda: ex(Pd, out=K64, tau=tau))
+        st64 = ex.stats
+        Km = torch.empty_like(Pd)
+        msm, _ = _event_ms(stream, lambda: ex(Pd, out=Km, tau=tau, precision=kx.KX_MIXED, split_threshold=SPLIT))
+        stm = ex.stats
+        Kl = torch.empty_like(Pd)
+        learned.learned_exchange(ex, Pd, model, tau, K=Kl, precision=kx.KX_MIXED, split_threshold=SPLIT)
+        msl, (_, info) = _event_ms(stream, lambda: learned.learned_exchange(
+            ex, Pd, model, tau, K=Kl, precision=kx.KX_MIXED, split_threshold=SPLIT))
+        row = {"system": name, "n_fn": s.n_fn, "tau": tau,
+               "leaf_quartets": st64.n_leaf_quartets, "leaf_quartets_learned": info["leaf_quartets_kept"],
+               "leaf_quartets_cullable": info["cullable"],
+               "shell_quartets": stm.n_shell_quartets, "shell_quartets_learned": info["shell_quartets"],
+               "fp64_ms": ms64, "mixed_ms": msm, "learned_mixed_ms": msl,
+               "speedup_mixed": ms64 / msm, "speedup_learned_mixed": ms64 / msl,
+               "max_abs_dK_mixed_vs_fp64": float((Km - K64).abs().max().item()),
+               "max_abs_dK_learned_vs_fp64": float((Kl - K64).abs().max().item())}
+        evals.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        ex.close()
+    print(json.dumps({"study": "learned", "tau": tau, "split_threshold": SPLIT,
+                      "training": {"systems": [t[0] for t in train_sets], "traces": int(len(tr.targets)),
+                                   "epochs": args.epochs, "loss_first": model.losses[0],
+                                   "loss_last": model.losses[-1], "residual_std_decades": model.residual_std,
+                                   "trace_s": t_tr, "train_s": t_train},
+                      "evaluation": evals}), flush=True)
 
 
 def main():
@@ -609,8 +807,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-symmetric", action="store_true",
                     help="build every K block instead of the A <= C half and its mirror")
+    ap.add_argument("--leaf-max", type=int, default=10, help="bisection leaf size in functions (Eq. 1)")
+    ap.add_argument("--study", choices=["sweep", "learned"], default=None,
+                    help="instead of the benchmark line: the (H2O)_n scaling sweep, or the learned-culling "
+                         "evaluation (one JSON line each, per-point lines on stderr)")
+    ap.add_argument("--sweep-n", default=",".join(map(str, SWEEP_N)))
+    ap.add_argument("--sweep-bases", default="medium,small")
+    ap.add_argument("--epochs", type=int, default=300)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.study == "sweep":
+        run_sweep(args)
+    elif args.study == "learned":
+        run_learned(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)

@@ -141,6 +141,17 @@ int kx_exchange(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o,
 int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts* o,
                      double* K_host, int64_t ldk, kx_stats* st);
 
+/* Survivor counts of one build without building it: the traversal (Eqs.
+ * 7-8) and the shell-level screen of kx_exchange for the same P and
+ * options, but no integral is evaluated and K is not touched.  Fills
+ * n_leaf_quartets, n_tasks, depth, n_candidates, n_shell_quartets,
+ * n_shell_quartets_fp64 (KX_MIXED: those above split_threshold) and
+ * flops_fp64/flops_fp32 (the ERI stage's algorithmic FLOPs), exactly as the
+ * build would report them; the time fields hold the traversal and screen.
+ * P: DEVICE, as for kx_exchange (ldp >= n_fn), or packed per system with
+ * ldp = 0 on a batch context.  st is required.  Synchronous. */
+int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats* st);
+
 /* ------------------------------------------------------------------------
  * Batches of independent systems (a growth direction beyond the paper: many
  * uneven systems in one traversal and one set of class-kernel launches).

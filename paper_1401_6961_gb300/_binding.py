@@ -21,7 +21,7 @@ ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "K
 
 # every entry point declared in include/kx.h
 EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", "kx_exchange",
-           "kx_exchange_host", "kx_create_batch", "kx_exchange_batch", "kx_exchange_batch_host",
+           "kx_exchange_host", "kx_count", "kx_create_batch", "kx_exchange_batch", "kx_exchange_batch_host",
            "kx_packed_size", "kx_autotune", "kx_get_launch_shapes", "kx_set_launch_shape", "kx_graph_plan", "kx_graph_launch",
            "kx_n_functions", "kx_get_order", "kx_get_leaves", "kx_get_worklist",
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
                               ctypes.POINTER(kx_stats)]
     L.kx_exchange_host.argtypes = [vp, _f64p, ctypes.c_int64, ctypes.POINTER(kx_opts), _f64p,
                                    ctypes.c_int64, ctypes.POINTER(kx_stats)]
+    L.kx_count.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), ctypes.POINTER(kx_stats)]
     L.kx_create_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(kx_basis), ctypes.c_int, vp]
     L.kx_exchange_batch.argtypes = [vp, vp, ctypes.POINTER(kx_opts), vp, ctypes.POINTER(kx_stats)]
     L.kx_exchange_batch_host.argtypes = [vp, _f64p, ctypes.POINTER(kx_opts), _f64p, ctypes.POINTER(kx_stats)]
@@ -274,6 +275,13 @@ def kx_exchange_host(ctx, P: np.ndarray, opts: kx_opts, K: np.ndarray) -> kx_sta
     st = kx_stats()
     _check(ctx, load().kx_exchange_host(ctx, P.ctypes.data_as(_f64p), P.strides[0] // 8, ctypes.byref(opts),
                                         K.ctypes.data_as(_f64p), K.strides[0] // 8, ctypes.byref(st)))
+    return st
+
+
+def kx_count(ctx, P_ptr: int, ldp: int, opts: kx_opts) -> kx_stats:
+    """Survivor counts of a build (device P; ldp = 0 for a batch's packed P)."""
+    st = kx_stats()
+    _check(ctx, load().kx_count(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts), ctypes.byref(st)))
     return st
 
 
@@ -468,6 +476,12 @@ class Exchange:
         K = np.zeros_like(P)
         self.stats = kx_exchange_host(self.ctx, np.ascontiguousarray(P), kx_default_opts(**opts), K)
         return K
+
+    def count(self, P, **opts) -> kx_stats:
+        """Survivor counts of the build ``self(P, **opts)`` without building K."""
+        import torch
+        assert P.is_cuda and P.dtype == torch.float64 and P.stride(1) == 1 and P.shape == (self.n_fn, self.n_fn)
+        return kx_count(self.ctx, P.data_ptr(), P.stride(0), kx_default_opts(**opts))
 
     def autotune(self, P, out=None, **opts):
         """One build (P, K dense and contiguous) that also tunes the class

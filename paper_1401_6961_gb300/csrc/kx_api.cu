@@ -324,6 +324,25 @@ int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts
     return KX_OK;
 }
 
+int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P || !o || !st) return set_err(c, KX_EINVAL, "null argument");
+    if (c->n_sys == 1 ? ldp < c->n_fn : ldp != 0)
+        return set_err(c, KX_EINVAL, "ldp must be >= n_fn (0 for the packed P of a batch)");
+    if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
+    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
+        return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
+    if (o->symmetric != 0 && o->symmetric != 1) return set_err(c, KX_EINVAL, "symmetric must be 0 or 1");
+    if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    std::memset(st, 0, sizeof(*st));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
+    return drive(c, RUN_COUNT, P, ldp, o, nullptr, 0, st, nullptr, 0);
+}
+
 int kx_exchange_batch(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st) {
     KX_TRY(check_ctx(c));
     return exchange_impl(c, P, 0, o, K, 0, st);

@@ -350,7 +350,8 @@ int traverse_and_evaluate(kx_ctx* c, const double* P, int64_t ldp, const kx_opts
                           double* K, int64_t ldk, kx_stats* st);  // kx_traverse.cu
 // what one driver call does: the whole build, the traversal alone (the leaf
 // list is kept), or the ERI stage over an explicit device leaf list
-enum { RUN_EXCHANGE = 0, RUN_TRAVERSE = 1, RUN_EVALUATE = 2 };
+// RUN_COUNT: traversal and the shell screen's count pass only (no records, no K)
+enum { RUN_EXCHANGE = 0, RUN_TRAVERSE = 1, RUN_EVALUATE = 2, RUN_COUNT = 3 };
 int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
           kx_stats* st, const Task* list, int64_t nlist);
 void drop_graph(kx_ctx* c);

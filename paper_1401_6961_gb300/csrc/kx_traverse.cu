@@ -332,6 +332,7 @@ struct Run {
     Timer* tm;
     int64_t rec_limit;
     double eri_max_ms;
+    bool count_only;
 };
 
 int process_leaves(Run& r, const Task* leaves, int64_t n);
@@ -418,7 +419,7 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     int64_t total = 0;
     KX_TRY(exclusive_scan(c, bin, binoff, nbin, &total));
     c->plan_max_rec = std::max(c->plan_max_rec, total);
-    if (total > r.rec_limit && n > 1) {
+    if (total > r.rec_limit && n > 1 && !r.count_only) {
         // too many records for one pass: halve the leaf list
         int64_t h0 = n / 2;
         KX_TRY(process_leaves(r, leaves, h0));
@@ -435,6 +436,17 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     for (int s = 0; s < 2 * NCLASS; ++s) {
         h[s] = (unsigned long long)(off[s + 1] - off[s]);
         endv[s] = (unsigned long long)off[s + 1];
+    }
+    if (r.count_only) {
+        for (int s = 0; s < 2 * NCLASS; ++s) {
+            const double f = class_flops(s % NCLASS) * (double)h[s];
+            if (s < NCLASS) r.st->flops_fp64 += f; else r.st->flops_fp32 += f;
+            c->prof_n[s] += (int64_t)h[s];
+        }
+        r.st->n_shell_quartets += total;
+        for (int s = 0; s < NCLASS; ++s) r.st->n_shell_quartets_fp64 += (int64_t)h[s];
+        r.st->n_chunks++;
+        return KX_OK;
     }
     KX_TRY(grow(c, &c->d_rec, &c->rec_cap, (size_t)total));
     KX_CUDA(c, cudaMemcpyAsync(c->d_counters + CTR_END, endv, sizeof(endv), cudaMemcpyHostToDevice, c->stream));
@@ -494,11 +506,13 @@ int keep_leaves(kx_ctx* c, const Task* leaves, int64_t n) {
 int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
           kx_stats* st, const Task* list, int64_t nlist) {
     const int D = c->depth;
-    const bool evaluate = mode != RUN_TRAVERSE;
+    const bool evaluate = mode == RUN_EXCHANGE || mode == RUN_EVALUATE;
+    // the leaf quartets go through the shell screen (count pass only for RUN_COUNT)
+    const bool screen = evaluate || mode == RUN_COUNT;
     // an eager build may move the buffers a captured plan points to
     drop_graph(c);
     Timer tm{c, {}};
-    Run r{c, P, ldp, o, K, ldk, st, &tm, 0, 0.0};
+    Run r{c, P, ldp, o, K, ldk, st, &tm, 0, 0.0, mode == RUN_COUNT};
     // record budget per pass: the caller's, else 2^30 records (8 GB) or a
     // quarter of the free device memory, whichever is smaller
     size_t fr = 0, tot = 0;
@@ -543,7 +557,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     }
     if (evaluate) KX_TRY(pair_tables(c, o->tau, o->shell_screen != 0));
     const bool keep = mode == RUN_TRAVERSE || (mode == RUN_EXCHANGE && o->keep_worklist);
-    if (mode != RUN_EVALUATE) {
+    if (mode == RUN_EXCHANGE || mode == RUN_TRAVERSE) {
         c->keep_n = 0;
         c->keep_valid = false;
     }
@@ -583,7 +597,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
         st->n_tasks[0] = nk;
         st->n_leaf_quartets = nk;
         if (keep) KX_TRY(keep_leaves(c, c->d_front[0], nk));
-        if (evaluate) KX_TRY(process_leaves(r, c->d_front[0], nk));
+        if (screen) KX_TRY(process_leaves(r, c->d_front[0], nk));
     } else {
         for (int k = 0; k < D; ++k) {
             const int32_t* child = c->d_node_child + c->levels[k].off;
@@ -642,7 +656,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
                                                           c->d_front[1 - cur], nullptr);
                 c->launches++;
                 if (keep) KX_TRY(keep_leaves(c, c->d_front[1 - cur], o1 - o0));
-                if (evaluate) KX_TRY(process_leaves(r, c->d_front[1 - cur], o1 - o0));
+                if (screen) KX_TRY(process_leaves(r, c->d_front[1 - cur], o1 - o0));
             }
         }
     }

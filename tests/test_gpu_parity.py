@@ -177,6 +177,37 @@ def test_random_shells_fp64_shared_memory_variant(kx, seed):
     ex.close()
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(symmetric=1), dict(shell_screen=0),
+                                  dict(precision=1, split_threshold=1e-4),
+                                  dict(precision=1, split_threshold=1e-4, symmetric=1)])
+def test_count_equals_build_and_oracle(kx, opts):
+    """kx_count reports the survivors of the build it stands for without
+    building K: the same counts as the build, and (every K block, shell
+    screen on) the oracle's leaf worklist length and shell-quartet count."""
+    import torch
+    big = wl.water64(2)
+    w3 = wl.build_system("w3", big.symbols[:9], big.xyz[:9] / wl.BOHR_PER_ANGSTROM, "medium")
+    for sys_, P in (wl.workload("water4"), (w3, wl.density(w3, 3003))):
+        for tau in (1e-10, 1e-6):
+            ex = kx.Exchange(sys_)
+            Pd = torch.from_numpy(np.ascontiguousarray(P)).cuda()
+            c = ex.count(Pd, tau=tau, **opts)
+            ex(Pd, tau=tau, **opts)
+            b = ex.stats
+            assert c.n_leaf_quartets == b.n_leaf_quartets > 0
+            assert c.n_shell_quartets == b.n_shell_quartets > 0
+            assert c.n_shell_quartets_fp64 == b.n_shell_quartets_fp64
+            assert c.n_candidates == b.n_candidates
+            assert c.depth == b.depth and list(c.n_tasks) == list(b.n_tasks)
+            assert c.flops_fp64 == pytest.approx(b.flops_fp64, rel=1e-12)
+            assert c.flops_fp32 == pytest.approx(b.flops_fp32, rel=1e-12)
+            if not opts.get("symmetric") and opts.get("shell_screen", 1):
+                _, work, nq, _, _ = oracle.exchange_screened(sys_, P, tau)
+                assert c.n_leaf_quartets == len(work)
+                assert c.n_shell_quartets == nq
+            ex.close()
+
+
 def test_medium_basis_three_waters(kx):
     big = wl.water64(2)
     s = wl.build_system("w3", big.symbols[:9], big.xyz[:9] / wl.BOHR_PER_ANGSTROM, "medium")
@@ -332,3 +363,24 @@ def test_water64_mixed_rows(w64):
     assert np.abs(Km[idx] - Kref[idx]).max() <= TOLMIX
     assert np.abs(Km - K64).max() <= TOLMIX
     assert stm.n_shell_quartets == st64.n_shell_quartets
+
+
+def test_sweep_member_water128_mixed_rows(kx):
+    """A member of the (H2O)_n scaling sweep, (H2O)_128 (3968 functions),
+    tau = 1e-8, built as the benchmark builds (mixed, split 5e-4,
+    symmetric): sampled K-row shells (one of them d) against the oracle."""
+    import torch
+    sys_ = wl.water_sweep(128, "medium")
+    P = wl.density(sys_, 5128)
+    ex = kx.Exchange(sys_)
+    Pd = torch.from_numpy(P).cuda()
+    K = ex(Pd, tau=1e-8, precision=kx.KX_MIXED, split_threshold=5e-4, symmetric=1).cpu().numpy()
+    assert ex.stats.n_shell_quartets_fp64 > 0
+    ex.close()
+    rows = [int(np.random.default_rng(128).integers(sys_.n_shell)), int(np.nonzero(sys_.shell_l == 2)[0][17])]
+    Kref, *_ = oracle.exchange_screened(sys_, P, 1e-8, rows=rows)
+    off = sys_.shell_offset
+    idx = np.concatenate([np.arange(off[r], off[r + 1]) for r in rows])
+    assert np.abs(K[idx] - Kref[idx]).max() <= TOLMIX
+    # symmetric build: the mirrored columns agree as well
+    assert np.abs(K[:, idx] - Kref[idx].T).max() <= TOLMIX
