@@ -5,7 +5,7 @@ One step = one complete exchange build K = sum (mu lam|nu sig) P_{lam sig}
 (P norms and pyramid, pair tables, hextree traversal with the Eq. 8 metric
 query, shell screen, ERI evaluation and contraction) of the seeded
 (H2O)_64 cluster at 1 g/cm^3, medium basis (1984 functions, 1024 shells),
-tau = 1e-10, replayed from one captured CUDA graph (after an untimed
+tau = 1e-10, leaves of at most 16 functions, replayed from one captured CUDA graph (after an untimed
 autotuning build and the capture).  The headline is the mixed-precision
 build (FP32 ERIs for quartets with beta <= split, FP64 above), next to the
 plain FP64 build of the same system; both stay within max|dK| <= 1e-8 of
@@ -37,6 +37,7 @@ WORKLOADS = ("water64", "water16", "batch256")
 BATCH_TAU = 1e-8
 TAU = 1e-10
 SPLIT = 5e-4          # measured max|dK| vs FP64: 3.0e-9 on (H2O)64, 1.7e-9 on the batch
+BENCH_LEAF = 16       # leaf size of the benchmark builds (fastest of 10, 16, 20, 32 on (H2O)64)
 L2_FLUSH_BYTES = 256 << 20
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
@@ -154,7 +155,7 @@ def measured_peak(name: str):
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(sys_, P, n_rows: int, seed: int = 1):
+def oracle_sample(sys_, P, n_rows: int, seed: int = 1, leaf_max: int = 10):
     """Exact screened K rows of n_rows sampled shells; returns (seconds,
     extrapolated K-builds/s, threads, description)."""
     import numpy as np
@@ -163,7 +164,7 @@ def oracle_sample(sys_, P, n_rows: int, seed: int = 1):
     oracle.build()
     rows = [int(x) for x in np.random.default_rng(seed).choice(sys_.n_shell, size=n_rows, replace=False)]
     t0 = time.perf_counter()
-    oracle.exchange_screened(sys_, P, TAU, rows=rows)
+    oracle.exchange_screened(sys_, P, TAU, leaf_max=leaf_max, rows=rows)
     dt = time.perf_counter() - t0
     full = dt * sys_.n_shell / n_rows
     desc = (f"oracle (FP64 C, OpenMP) screened exchange of {n_rows} sampled K-row shells of "
@@ -171,7 +172,7 @@ def oracle_sample(sys_, P, n_rows: int, seed: int = 1):
     return dt, 1.0 / full, oracle.num_threads(), desc
 
 
-def oracle_batch_sample(systems, dens, n_sys: int, n_rows: int, seed: int = 1):
+def oracle_batch_sample(systems, dens, n_sys: int, n_rows: int, seed: int = 1, leaf_max: int = 10):
     """Exact screened K rows of n_rows shells in each of n_sys sampled
     systems of a batch, extrapolated to every shell of every system."""
     import numpy as np
@@ -186,7 +187,7 @@ def oracle_batch_sample(systems, dens, n_sys: int, n_rows: int, seed: int = 1):
         s = systems[int(y)]
         rows = [int(x) for x in rng.choice(s.n_shell, size=n_rows, replace=False)]
         t0 = time.perf_counter()
-        oracle.exchange_screened(s, dens[int(y)], BATCH_TAU, rows=rows)
+        oracle.exchange_screened(s, dens[int(y)], BATCH_TAU, leaf_max=leaf_max, rows=rows)
         dt = time.perf_counter() - t0
         t_all += dt
         est += dt * s.n_shell / n_rows
@@ -206,14 +207,15 @@ def run_reference(args):
         rates = []
         threads, desc = 1, ""
         for i in range(args.warmup + args.steps):
-            dt, rate, threads, desc = oracle_batch_sample(systems, dens, 32, 4 * args.ref_rows, seed=100 + i)
+            dt, rate, threads, desc = oracle_batch_sample(systems, dens, 32, 4 * args.ref_rows, seed=100 + i,
+                                                          leaf_max=args.leaf_max)
             if i >= args.warmup:
                 rates.append(rate)
         v = statistics.mean(rates)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": batch_config(systems, "fp64"),
+                "data": "synthetic", "config": batch_config(systems, "fp64", leaf_max=args.leaf_max),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -225,7 +227,7 @@ def run_reference(args):
     threads = 1
     desc = ""
     for i in range(args.warmup + args.steps):
-        dt, rate, threads, desc = oracle_sample(sys_, P, args.ref_rows, seed=100 + i)
+        dt, rate, threads, desc = oracle_sample(sys_, P, args.ref_rows, seed=100 + i, leaf_max=args.leaf_max)
         if i >= args.warmup:
             times.append(dt)
             rates.append(rate)
@@ -233,7 +235,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(sys_, "fp64", args.workload),
+            "data": "synthetic", "config": workload_config(sys_, "fp64", args.workload, leaf_max=args.leaf_max),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -251,13 +253,13 @@ def workload_config(sys_, precision, name, symmetric=True, leaf_max=10):
             "parallelism": "replicas"}
 
 
-def batch_config(systems, precision, symmetric=True):
+def batch_config(systems, precision, symmetric=True, leaf_max=10):
     nw = [s.n_atom // 3 for s in systems]
     return {"workload": f"{len(systems)} independent water clusters of 4-48 molecules (drawn {min(nw)}-{max(nw)}), "
                         f"1 g/cm^3, small even-tempered basis (13 functions per water; "
                         f"{sum(s.n_fn for s in systems)} functions in all), each with its own density, "
                         f"tau={BATCH_TAU:g}",
-            "name": "batch256", "systems": len(systems), "tau": BATCH_TAU, "leaf_max": 10,
+            "name": "batch256", "systems": len(systems), "tau": BATCH_TAU, "leaf_max": leaf_max,
             "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
             "shell_screen": True, "symmetric": bool(symmetric),
             "launch": "one captured CUDA graph per batch build (autotuned class-kernel shapes)",
@@ -286,7 +288,7 @@ def run_batch(args):
     kx.load()
     systems, dens = wl.batch_workload()
     stream = torch.cuda.current_stream(dev)
-    bx = kx.BatchExchange(systems, device=local, stream=stream)
+    bx = kx.BatchExchange(systems, device=local, stream=stream, leaf_max=args.leaf_max)
     Pd = torch.from_numpy(np.concatenate([d.ravel() for d in dens])).to(dev)
     Kd = torch.empty_like(Pd)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -367,14 +369,14 @@ def run_batch(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        dt, rate, thr, desc = oracle_batch_sample(systems, dens, 32, 4 * args.ref_rows)
+        dt, rate, thr, desc = oracle_batch_sample(systems, dens, 32, 4 * args.ref_rows, leaf_max=args.leaf_max)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": batch_config(systems, "mixed", sym),
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": batch_config(systems, "mixed", sym, args.leaf_max),
             "quartets_per_s": ws * st.n_shell_quartets / (ms_step * 1e-3),
             "shell_quartets": st.n_shell_quartets, "leaf_quartets": st.n_leaf_quartets,
             "shell_quartets_fp64": st.n_shell_quartets_fp64,
@@ -559,7 +561,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        dt, rate, thr, desc = oracle_sample(sys_, P, args.ref_rows)
+        dt, rate, thr, desc = oracle_sample(sys_, P, args.ref_rows, leaf_max=args.leaf_max)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
 
     if rank == 0:
@@ -615,8 +617,9 @@ def run_ours(args):
 SWEEP_N = (64, 128, 256, 512)
 SWEEP_TAU = (1e-10, 1e-8, 1e-6)
 SWEEP_BUILD_S = 25.0      # time a build only when the count predicts at most this many seconds
-SWEEP_MAX_SHELL_Q = 2e12  # counts (traversal + count pass of the screen) stay within about 20 s
-SWEEP_MAX_LEAF_Q = 1e10   # and the frontier before the last level within a few tens of GB
+SWEEP_MAX_SHELL_Q = 2e12  # counts (traversal + count pass of the screen) stay within about 30 s
+SWEEP_MAX_LEAF_Q = 1.5e10  # and the frontier before the last level within a few tens of GB
+SWEEP_GROWTH = 2.5        # predicted survivors grow as n_fn^2.5 (measured: 1.7-2.6)
 RATE_MIXED, RATE_FP64 = 6e9, 1e9   # shell quartets/s of the (H2O)64 builds, for that prediction
 
 
@@ -648,17 +651,18 @@ def run_sweep(args):
     stream = torch.cuda.current_stream(dev)
     bases = [b.strip() for b in args.sweep_bases.split(",") if b.strip()]
     ns = [int(x) for x in args.sweep_n.split(",")]
+    taus_all = [float(x) for x in args.sweep_taus.split(",")]
     rows = []
     last = {}
     for basis in bases:
         for nw in ns:
             sys_ = wl.water_sweep(nw, basis)
             taus = []
-            for tau in SWEEP_TAU:
+            for tau in taus_all:
                 prev = last.get((basis, tau))
                 if prev is not None:
-                    # cubic growth from the previous size: a generous prediction
-                    g = (sys_.n_fn / prev[0]) ** 3
+                    # growth from the previous size, above the measured exponents
+                    g = (sys_.n_fn / prev[0]) ** SWEEP_GROWTH
                     if prev[1] * g > SWEEP_MAX_SHELL_Q or prev[2] * g > SWEEP_MAX_LEAF_Q:
                         rows.append({"basis": basis, "n_water": nw, "n_fn": sys_.n_fn, "tau": tau,
                                      "skipped": f"predicted more than {SWEEP_MAX_SHELL_Q:.0e} shell quartets or "
@@ -669,7 +673,7 @@ def run_sweep(args):
                 continue
             P = wl.density(sys_, 5000 + nw)
             t0 = time.perf_counter()
-            ex = kx.Exchange(sys_, device=0, stream=stream)
+            ex = kx.Exchange(sys_, device=0, stream=stream, leaf_max=args.leaf_max)
             setup_s = time.perf_counter() - t0
             Pd = torch.from_numpy(P).to(dev)
             del P
@@ -706,7 +710,7 @@ def run_sweep(args):
     # growth exponents: least squares of log(survivors) against log(n_fn)
     fits = []
     for basis in bases:
-        for tau in SWEEP_TAU:
+        for tau in taus_all:
             pts = [(r["n_fn"], r["shell_quartets"], r["leaf_quartets"]) for r in rows
                    if r["basis"] == basis and r["tau"] == tau and r.get("shell_quartets", 0) > 0]
             if len(pts) < 2:
@@ -718,7 +722,8 @@ def run_sweep(args):
                          "exponent_n_lg_n": float(np.polyfit(x, np.log([p[0] * math.log2(p[0]) for p in pts]),
                                                              1)[0])})
     print(json.dumps({"study": "sweep", "workload": "(H2O)_n at 1 g/cm^3, n = " + ",".join(map(str, ns)),
-                      "split_threshold": SPLIT, "leaf_max": 10, "points": rows, "fits": fits}), flush=True)
+                      "split_threshold": SPLIT, "leaf_max": args.leaf_max, "points": rows, "fits": fits}),
+          flush=True)
 
 
 def run_learned(args):
@@ -807,12 +812,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-symmetric", action="store_true",
                     help="build every K block instead of the A <= C half and its mirror")
-    ap.add_argument("--leaf-max", type=int, default=10, help="bisection leaf size in functions (Eq. 1)")
+    ap.add_argument("--leaf-max", type=int, default=BENCH_LEAF,
+                    help="bisection leaf size in functions (Eq. 1); the paper's CPU code used 10")
     ap.add_argument("--study", choices=["sweep", "learned"], default=None,
                     help="instead of the benchmark line: the (H2O)_n scaling sweep, or the learned-culling "
                          "evaluation (one JSON line each, per-point lines on stderr)")
     ap.add_argument("--sweep-n", default=",".join(map(str, SWEEP_N)))
     ap.add_argument("--sweep-bases", default="medium,small")
+    ap.add_argument("--sweep-taus", default=",".join(map(str, SWEEP_TAU)))
     ap.add_argument("--epochs", type=int, default=300)
     args = ap.parse_args()
     if args.study == "sweep":

@@ -156,7 +156,7 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
         const int ns = sg.n;
         const bool diag = p.sym && t.a == t.c;   // then a0 == c0
         const Div md(nd), mb(nb), mc(nc);
-        if (na <= STAGE && nb <= STAGE && nc <= STAGE && nd <= STAGE && total < 65536) {
+        if (na <= STAGE && nb <= STAGE && nc <= STAGE && nd <= STAGE && total <= 65536) {
             // stage the leaf quartet's log tables and pair classes
             __syncwarp();
             for (int k = lane; k < na * nb; k += 32) {

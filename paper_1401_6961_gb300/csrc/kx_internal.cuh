@@ -273,6 +273,9 @@ struct kx_ctx {
     bool tuned[2 * kx::NCLASS] = {};
     // what the last eager build saw (sizes for a captured plan)
     int64_t plan_max_rec = 0;             // largest record count of one leaf chunk
+    double rec_per_leaf = 48.0;           // shell-quartet records per leaf quartet (last build, with margin):
+                                          // sizes the leaf chunks of eager builds
+    int64_t last_lq = 1 << 16;            // leaf quartets per chunk of the last eager build
     uint8_t plan_active[2 * kx::NCLASS] = {};
     // autotuning inside an eager build (kx_autotune)
     bool tuning = false;

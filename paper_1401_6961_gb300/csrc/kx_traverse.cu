@@ -420,10 +420,14 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     KX_TRY(exclusive_scan(c, bin, binoff, nbin, &total));
     c->plan_max_rec = std::max(c->plan_max_rec, total);
     if (total > r.rec_limit && n > 1 && !r.count_only) {
-        // too many records for one pass: halve the leaf list
-        int64_t h0 = n / 2;
-        KX_TRY(process_leaves(r, leaves, h0));
-        return process_leaves(r, leaves + h0, n - h0);
+        // too many records for one pass: pieces of about 0.9 rec_limit records
+        // each (a piece that still overflows splits again)
+        const int64_t m = std::min<int64_t>(n, std::max<int64_t>(2, (int64_t)(1.1 * (double)total / r.rec_limit) + 1));
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t i0 = n * i / m, i1 = n * (i + 1) / m;
+            if (i1 > i0) KX_TRY(process_leaves(r, leaves + i0, i1 - i0));
+        }
+        return KX_OK;
     }
     if (total == 0) return KX_OK;
     // stream s starts at binoff[s * nb]
@@ -513,14 +517,18 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     drop_graph(c);
     Timer tm{c, {}};
     Run r{c, P, ldp, o, K, ldk, st, &tm, 0, 0.0, mode == RUN_COUNT};
-    // record budget per pass: the caller's, else 2^30 records (8 GB) or a
-    // quarter of the free device memory, whichever is smaller
+    // record budget per pass: the caller's, else 2^31 - 8192 records (16 GB;
+    // the class kernels' record slots are 32-bit) or 40 % of the free device
+    // memory, whichever is smaller
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    int64_t lim = (int64_t)std::min<size_t>((size_t)1 << 30, fr / 4 / sizeof(Quartet));
+    const int64_t lim = std::min<int64_t>(((int64_t)1 << 31) - 8192, (int64_t)(0.4 * (double)fr / sizeof(Quartet)));
     r.rec_limit = o->chunk_records > 0 ? o->chunk_records : std::max<int64_t>(lim, 1 << 20);
-    r.rec_limit = std::min<int64_t>(r.rec_limit, (int64_t)1 << 31);   // record slots are 32-bit in the binning
-    const int64_t lq_cap = std::max<int64_t>(r.rec_limit / 48, 1 << 16);
+    r.rec_limit = std::min<int64_t>(r.rec_limit, ((int64_t)1 << 31) - 8192);
+    // leaf quartets per chunk: a pass's worth of records at the record rate
+    // per leaf quartet of the previous build
+    const int64_t lq_cap = std::max<int64_t>((int64_t)((double)r.rec_limit / std::max(4.0, c->rec_per_leaf)), 1 << 16);
+    c->last_lq = lq_cap;
 
     c->launches = 0;
     c->plan_max_rec = 0;
@@ -662,6 +670,8 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     }
     if (keep) c->keep_valid = true;
     if (evaluate && o->symmetric) KX_TRY(mirror_k(c, K));
+    if (screen && st->n_leaf_quartets > 0 && st->n_shell_quartets > 0)
+        c->rec_per_leaf = 1.25 * (double)st->n_shell_quartets / (double)st->n_leaf_quartets;
     return finish_run(c, st, tm, D);
 }
 
@@ -998,12 +1008,11 @@ int graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double h
     for (int k = 0; k < D; ++k) maxpar = std::max<int64_t>(maxpar, st->n_tasks[k]);
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    const int64_t rec_limit = std::min<int64_t>((int64_t)1 << 30, (int64_t)(fr / 4 / sizeof(Quartet)));
     // records of one chunk: the class-kernel slots are 32-bit, and the
     // records should leave most of the memory to the rest
     const int64_t budget = std::min<int64_t>(((int64_t)1 << 31) - 8192, (int64_t)(0.4 * fr / sizeof(Quartet)));
     GraphCaps cap;
-    cap.lq = std::max<int64_t>(rec_limit / 48, 1 << 16);   // the eager build's chunks
+    cap.lq = c->last_lq;   // the eager build's chunks
     cap.fcap = (int64_t)(maxlev * m) + 64;
     cap.mcap = (int64_t)(maxpar * m) + 64;
     const double need = c->plan_max_rec * m + 4096;

@@ -106,12 +106,17 @@ def test_batch_symmetric_and_graph(kx):
     bx.close()
 
 
+BENCH_LEAF = 16   # bisection leaf size of the benchmark builds
+
+
 def test_water64_symmetric_mixed_rows(kx):
-    """The benchmark system in the benchmark's launch configuration (tuned
-    shapes, captured build replayed, split 5e-4, symmetric): sampled K rows."""
+    """The benchmark system in the benchmark's launch configuration (leaf
+    size 16, tuned shapes, captured build replayed, split 5e-4, symmetric):
+    sampled K rows against the oracle at the same leaf size, and the leaf
+    worklist of those rows against the oracle's traversal."""
     import torch
     sys_, P = wl.workload("water64")
-    ex = kx.Exchange(sys_)
+    ex = kx.Exchange(sys_, leaf_max=BENCH_LEAF)
     Pd = torch.from_numpy(P).cuda()
     Kd = torch.empty_like(Pd)
     opts = dict(tau=1e-10, precision=kx.KX_MIXED, split_threshold=5e-4, symmetric=1)
@@ -122,10 +127,20 @@ def test_water64_symmetric_mixed_rows(kx):
     torch.cuda.synchronize()
     K = Kd.cpu().numpy()
     rows = [int(x) for x in np.random.default_rng(65).choice(sys_.n_shell, size=3, replace=False)]
-    Kref, *_ = oracle.exchange_screened(sys_, P, 1e-10, rows=rows)
+    Kref, wref, nq, tree, s2 = oracle.exchange_screened(sys_, P, 1e-10, leaf_max=BENCH_LEAF, rows=rows)
     off = sys_.shell_offset
     idx = np.concatenate([np.arange(off[r], off[r + 1]) for r in rows])
     assert np.abs(K[idx] - Kref[idx]).max() <= TOLMIX
     # the mirrored half: columns of the same rows
     assert np.abs(K[:, idx] - Kref[idx].T).max() <= TOLMIX
+    # the worklist of an eager build of the same configuration, restricted to
+    # the leaves that hold the sampled rows: the oracle's, with A <= C
+    ex(Pd, out=Kd, keep_worklist=1, **opts)
+    leaves, _ = ex.leaves()
+    pos = {int(s): i for i, s in enumerate(ex.order())}
+    aleaf = sorted({int(np.searchsorted(leaves[:, 1], pos[r], side="right")) for r in rows})
+    w = ex.worklist(aleaf)
+    half = wref[wref[:, 0] <= wref[:, 2]]
+    assert set(half[:, 0].tolist()) <= set(aleaf)
+    assert np.array_equal(_sorted(w), _sorted(half))
     ex.close()
