@@ -117,7 +117,7 @@ def kernel_name(kx, ctx, s: int) -> str:
     if s >= 81:
         return f"k_eri_big<{args}>"
     variant = int(kx.kx_get_launch_shapes(ctx)[2][s])
-    return f"k_eri_big64<{args}>" if variant == 1 else f"k_eri_rolled<{args},double>"
+    return {1: f"k_eri_big64<{args}>", 2: f"k_eri_big64p<{args}>"}.get(variant, f"k_eri_rolled<{args},double>")
 
 
 def barrier(ws: int) -> None:
@@ -504,6 +504,16 @@ def run_ours(args):
     peak32 = kx.kx_peak_probe(local, kx.KX_MIXED) / 1e3
     peak = peak64 if prec_dom == "fp64" else peak32
     eri_ms = float(prof["ms"].sum())
+    # every class stream of the eager builds, on stderr
+    streams = []
+    for s_ in range(162):
+        if prof["ms"][s_] > 0:
+            c_ = s_ % 81
+            streams.append({"stream": s_, "class": "({}{}|{}{})".format(*("spd"[x] for x in (
+                c_ // 27, (c_ // 9) % 3, (c_ // 3) % 3, c_ % 3))), "precision": "fp64" if s_ < 81 else "fp32",
+                "kernel": kernel_name(kx, ex.ctx, s_), "ms": float(prof["ms"][s_]), "quartets": int(prof["n"][s_]),
+                "tflops": float(prof["flops"][s_] / (prof["ms"][s_] * 1e-3) / 1e12)})
+    print(json.dumps({"eri_streams": streams}), file=sys.stderr, flush=True)
     # the ten costliest class streams of the eager builds
     top = []
     for s_ in np.argsort(-prof["ms"])[:10]:

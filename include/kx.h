@@ -198,12 +198,15 @@ int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stat
 /* Current launch shape of the 162 streams (threads per block; persistent
  * blocks per SM, 0 = one thread per quartet; kernel variant: 0 for every
  * stream except the FP64 classes with la+lb+lc+ld >= 7, where 0 is the
- * rolled kernel and 1 the shared-memory kernel).  Host arrays, may be NULL. */
+ * rolled kernel, 1 the shared-memory kernel and 2 the shared-memory kernel
+ * with the ket Hermite set pruned per ket component).  Host arrays, may be
+ * NULL. */
 int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm, int32_t* variant);
 
 /* Sets the launch shape of stream s = precision * 81 + class: threads a
- * multiple of 32 in [32, 256], blocks_per_sm >= 0, variant 0 or 1 (1 only
- * where two kernels exist).  KX_EINVAL otherwise.  Discards a captured plan. */
+ * multiple of 32 in [32, 256], blocks_per_sm >= 0, variant 0, 1 or 2 (1 and 2
+ * only where those kernels exist).  KX_EINVAL otherwise.  Discards a captured
+ * plan. */
 int kx_set_launch_shape(kx_ctx* c, int32_t s, int32_t threads, int32_t blocks_per_sm, int32_t variant);
 
 /* Captured build.  kx_graph_plan runs one kx_exchange_batch build (P, K

@@ -1317,7 +1317,9 @@ double eri_flops() {
 // The kernel of a class and precision: unrolled below ROLL_L; above it the
 // rolled kernel in FP64 and the shared-memory kernel in FP32.
 // variant 1 (large classes only): the shared-memory kernel; FP32 uses it by
-// default, FP64 when the autotuner finds it faster than the rolled kernel
+// default, FP64 when the autotuner finds it faster than the rolled kernel;
+// variant 2 (FP64 large classes): the shared-memory kernel with the ket set
+// pruned per nu
 template <int LA, int LB, int LC, int LD>
 EriKern eri_kernel(int prec, int variant) {
     if constexpr (LA + LB + LC + LD < ROLL_L) {
@@ -1325,8 +1327,9 @@ EriKern eri_kernel(int prec, int variant) {
     } else {
         if (prec == 1) return {&k_eri_big<LA, LB, LC, LD>, (int)sizeof(float) * big_slice<LA, LB, LC, LD>(), 1};
         if (variant == 1)
-            return {&k_eri_big64<LA, LB, LC, LD>, (int)sizeof(double) * nherm(LA + LB + LC + LD), 2};
-        return {&k_eri_rolled<LA, LB, LC, LD, double>, 0, 2};
+            return {&k_eri_big64<LA, LB, LC, LD>, (int)sizeof(double) * nherm(LA + LB + LC + LD), 3};
+        if (variant == 2) return eri_kernel_big64p(LA * 27 + LB * 9 + LC * 3 + LD);
+        return {&k_eri_rolled<LA, LB, LC, LD, double>, 0, 3};
     }
 }
 

@@ -368,10 +368,10 @@ int eri_fit_threads(const EriKern& k, int threads) {
 }
 
 int eri_prepare(kx_ctx* c, int s, int variant, const EriKern& k) {
-    if (k.smem_per_thread > 0 && !c->eri_smem_set[s][variant & 1]) {
+    if (k.smem_per_thread > 0 && !c->eri_smem_set[s][variant % 3]) {
         KX_CUDA(c, cudaFuncSetAttribute((const void*)k.k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         SMEM_BLOCK_MAX));
-        c->eri_smem_set[s][variant & 1] = true;
+        c->eri_smem_set[s][variant % 3] = true;
     }
     return KX_OK;
 }

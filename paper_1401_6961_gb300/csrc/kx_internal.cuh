@@ -268,7 +268,7 @@ struct kx_ctx {
     int eri_threads[2 * kx::NCLASS] = {};
     int eri_bpsm[2 * kx::NCLASS] = {};
     int eri_variant[2 * kx::NCLASS] = {};       // kernel variant of the stream
-    bool eri_smem_set[2 * kx::NCLASS][2] = {};  // dynamic shared memory limit raised, per variant
+    bool eri_smem_set[2 * kx::NCLASS][3] = {};  // dynamic shared memory limit raised, per variant
     int n_sm = 0;
     bool tuned[2 * kx::NCLASS] = {};
     // what the last eager build saw (sizes for a captured plan)
@@ -418,6 +418,8 @@ struct EriKern {
 };
 
 EriKern eri_kernel(int cls, int prec, int variant);   // kx_expand.cu, over the nine below
+// the ket-pruned FP64 kernel of a class with la+lb+lc+ld >= 7
+EriKern eri_kernel_big64p(int cls);
 EriKern eri_kernel_ab00(int cls, int prec, int variant);
 EriKern eri_kernel_ab01(int cls, int prec, int variant);
 EriKern eri_kernel_ab02(int cls, int prec, int variant);

@@ -157,10 +157,12 @@ def test_random_shells_all_classes_fp32(kx, seed):
     assert np.abs(K - K0).max() <= 2e-5 * np.abs(K0).max()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("seed", [1, 2])
-def test_random_shells_fp64_shared_memory_variant(kx, seed):
-    """The FP64 large classes through their second kernel (shared-memory R,
-    full Hermite sets), forced for every such class."""
+def test_random_shells_fp64_shared_memory_variant(kx, seed, variant):
+    """The FP64 large classes through their other kernels (shared-memory R
+    with full Hermite sets; the same with the ket set pruned per nu), forced
+    for every such class."""
     sys_ = wl.random_shells(9, seed, lmax=2, box=2.5)
     P = wl.density(sys_, 100 + seed)
     K0 = oracle.exchange_direct(sys_, P)
@@ -168,8 +170,10 @@ def test_random_shells_fp64_shared_memory_variant(kx, seed):
     ex = kx.Exchange(sys_, leaf_max=6)
     big = [c for c in range(81) if c // 27 + c // 9 % 3 + c // 3 % 3 + c % 3 >= 7]
     for c in big:
-        kx.kx_set_launch_shape(ex.ctx, c, 128, 0, 1)
-    assert kx.kx_get_launch_shapes(ex.ctx)[2][big].tolist() == [1] * len(big)
+        kx.kx_set_launch_shape(ex.ctx, c, 128, 0, variant)
+    assert kx.kx_get_launch_shapes(ex.ctx)[2][big].tolist() == [variant] * len(big)
+    with pytest.raises(kx.KxError):
+        kx.kx_set_launch_shape(ex.ctx, big[0], 128, 0, 3)   # three kernels per FP64 large class
     with pytest.raises(kx.KxError):
         kx.kx_set_launch_shape(ex.ctx, 0, 128, 0, 1)      # (ss|ss) has one kernel
     K = ex(torch.from_numpy(P).cuda(), tau=0.0).cpu().numpy()
