@@ -70,6 +70,7 @@ def test_null_context_calls(lib):
     import paper_1401_6961_gb300 as kx
     assert lib.kx_build_schwarz(None, 0.0) == kx.KX_EINVAL
     assert lib.kx_build_tree(None, 10, None) == kx.KX_EINVAL
+    assert lib.kx_count(None, None, 0, None, None) == kx.KX_EINVAL
     assert lib.kx_n_functions(None) == -1
     assert lib.kx_last_error(None) == b"null context"
     lib.kx_destroy(None)
