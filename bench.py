@@ -114,9 +114,9 @@ def kernel_name(kx, ctx, s: int) -> str:
     args = f"{la},{lb},{lc},{ld}"
     if la + lb + lc + ld < 7:
         return f"k_eri<{args},{'double' if s < 81 else 'float'}>"
-    if s >= 81:
-        return f"k_eri_big<{args}>"
     variant = int(kx.kx_get_launch_shapes(ctx)[2][s])
+    if s >= 81:
+        return f"k_eri_bigp<{args}>" if variant == 1 else f"k_eri_big<{args}>"
     return {1: f"k_eri_big64<{args}>", 2: f"k_eri_big64p<{args}>"}.get(variant, f"k_eri_rolled<{args},double>")
 
 

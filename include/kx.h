@@ -197,9 +197,10 @@ int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stat
 
 /* Current launch shape of the 162 streams (threads per block; persistent
  * blocks per SM, 0 = one thread per quartet; kernel variant: 0 for every
- * stream except the FP64 classes with la+lb+lc+ld >= 7, where 0 is the
+ * stream except the classes with la+lb+lc+ld >= 7, where FP64 has 0 the
  * rolled kernel, 1 the shared-memory kernel and 2 the shared-memory kernel
- * with the ket Hermite set pruned per ket component).  Host arrays, may be
+ * with the ket Hermite set pruned per ket component, and FP32 has 0 the
+ * shared-memory kernel and 1 its ket-pruned form).  Host arrays, may be
  * NULL. */
 int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm, int32_t* variant);
 

@@ -1314,18 +1314,20 @@ double eri_flops() {
     return f;
 }
 
-// The kernel of a class and precision: unrolled below ROLL_L; above it the
-// rolled kernel in FP64 and the shared-memory kernel in FP32.
-// variant 1 (large classes only): the shared-memory kernel; FP32 uses it by
-// default, FP64 when the autotuner finds it faster than the rolled kernel;
-// variant 2 (FP64 large classes): the shared-memory kernel with the ket set
-// pruned per nu
+// The kernel of a class and precision: unrolled below ROLL_L.  Above it
+// the FP64 classes have three variants (0 the rolled kernel, 1 the
+// shared-memory kernel with full Hermite sets, 2 the same with the ket set
+// pruned per nu) and the FP32 classes two (0 the shared-memory kernel, 1 the
+// same pruned per nu); the autotuner picks one per class.
 template <int LA, int LB, int LC, int LD>
 EriKern eri_kernel(int prec, int variant) {
     if constexpr (LA + LB + LC + LD < ROLL_L) {
         return {prec == 0 ? &k_eri<LA, LB, LC, LD, double> : &k_eri<LA, LB, LC, LD, float>, 0, 1};
     } else {
-        if (prec == 1) return {&k_eri_big<LA, LB, LC, LD>, (int)sizeof(float) * big_slice<LA, LB, LC, LD>(), 1};
+        if (prec == 1) {
+            if (variant == 1) return eri_kernel_bigp(LA * 27 + LB * 9 + LC * 3 + LD);
+            return {&k_eri_big<LA, LB, LC, LD>, (int)sizeof(float) * big_slice<LA, LB, LC, LD>(), 2};
+        }
         if (variant == 1)
             return {&k_eri_big64<LA, LB, LC, LD>, (int)sizeof(double) * nherm(LA + LB + LC + LD), 3};
         if (variant == 2) return eri_kernel_big64p(LA * 27 + LB * 9 + LC * 3 + LD);

@@ -418,8 +418,9 @@ struct EriKern {
 };
 
 EriKern eri_kernel(int cls, int prec, int variant);   // kx_expand.cu, over the nine below
-// the ket-pruned FP64 kernel of a class with la+lb+lc+ld >= 7
+// the ket-pruned FP64 and FP32 kernels of a class with la+lb+lc+ld >= 7
 EriKern eri_kernel_big64p(int cls);
+EriKern eri_kernel_bigp(int cls);
 EriKern eri_kernel_ab00(int cls, int prec, int variant);
 EriKern eri_kernel_ab01(int cls, int prec, int variant);
 EriKern eri_kernel_ab02(int cls, int prec, int variant);

@@ -157,6 +157,27 @@ def test_random_shells_all_classes_fp32(kx, seed):
     assert np.abs(K - K0).max() <= 2e-5 * np.abs(K0).max()
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_shells_fp32_pruned_variant(kx, seed):
+    """The FP32 large classes through their ket-pruned kernel, forced for
+    every such class (split above every bound: all quartets in FP32)."""
+    sys_ = wl.random_shells(9, seed, lmax=2, box=2.5)
+    P = wl.density(sys_, 100 + seed)
+    K0 = oracle.exchange_direct(sys_, P)
+    import torch
+    ex = kx.Exchange(sys_, leaf_max=6)
+    big = [81 + c for c in range(81) if c // 27 + c // 9 % 3 + c // 3 % 3 + c % 3 >= 7]
+    for s in big:
+        kx.kx_set_launch_shape(ex.ctx, s, 128, 0, 1)
+    assert kx.kx_get_launch_shapes(ex.ctx)[2][big].tolist() == [1] * len(big)
+    with pytest.raises(kx.KxError):
+        kx.kx_set_launch_shape(ex.ctx, big[0], 128, 0, 2)   # two kernels per FP32 large class
+    K = ex(torch.from_numpy(P).cuda(), tau=0.0, precision=kx.KX_MIXED, split_threshold=1e30).cpu().numpy()
+    assert ex.stats.n_shell_quartets_fp64 == 0
+    assert np.abs(K - K0).max() <= 2e-5 * np.abs(K0).max()
+    ex.close()
+
+
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_random_shells_fp64_shared_memory_variant(kx, seed, variant):
