@@ -84,3 +84,42 @@ def test_no_gpu_reports_cuda_error(lib):
     with pytest.raises(kx.KxError) as e:
         kx.kx_create(np.zeros((1, 3)), [0], [0], [1.0])
     assert e.value.code == kx.KX_ECUDA
+
+
+C_PROGRAM = r"""
+#include "kx.h"
+#include <stdio.h>
+int main(void) {
+    kx_opts o;
+    kx_stats st;
+    kx_default_opts(&o);
+    if (kx_count(NULL, NULL, 0, &o, &st) != KX_EINVAL) return 1;
+    if (kx_exchange(NULL, NULL, 0, &o, NULL, 0, NULL) != KX_EINVAL) return 2;
+    if (kx_n_functions(NULL) != -1) return 3;
+    printf("%s\n", kx_last_error(NULL));
+    kx_destroy(NULL);
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """The boundary is usable from C: the header compiles as strict C11 and a
+    C program links against libkx.so and calls it (null-context checks only:
+    no device work)."""
+    import shutil
+    import subprocess
+    from paper_1401_6961_gb300 import _binding
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_kx.c"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(_binding.library_path())
+    exe = tmp_path / "use_kx"
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lkx",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "null context"
