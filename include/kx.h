@@ -357,16 +357,26 @@ int kx_mlp_adam(float* params, const float* grad, float* m, float* v, float lr, 
  * written to `next` (DEVICE array with room for cap tasks) in the order the
  * traversal uses; *n_next (host) receives their number.  Starting from the
  * single task (0,0,0,0) at level 0 and calling it for levels 0 .. depth-1
- * yields the leaf-quartet worklist of kx_exchange for the same tau.
+ * yields the leaf-quartet worklist of kx_exchange for the same tau and the
+ * same `symmetric` option.  The root task itself is not tested, as in
+ * kx_exchange when depth >= 1; a tree of depth 0 (a single leaf) has no
+ * level to walk (KX_EINVAL), and there kx_exchange keeps the root task iff
+ * its own bound exceeds tau, a test left to the caller.
  *
  * Requirements: a tree (kx_build_tree) and the P norms of a previous
- * kx_exchange on this context (the norms of that call's P are used).
+ * kx_exchange on this context.  The norms of that call's P are used, and so
+ * is its `symmetric` option: after a symmetric build, a task whose K block
+ * is diagonal (A == C) keeps only the children with A' <= C', as in the
+ * traversal of that build.
  * Scratch: a file-scope device array of 4.5 MiB, holding counts,
  * offsets, masks and scan sums for up to KX_NOALLOC_MAX_TASKS tasks, that
  * every GPU which loads the library keeps until the process exits.  The
  * first call on a device (made current by the call) looks up that array's
  * device address; make that first call before any stream capture on the
- * device.  All calls share the array and it keeps the last call's contents
+ * device.  The address is kept for the life of the process: after a
+ * cudaDeviceReset (or any other teardown of the device's primary context)
+ * the kept address is stale, so do not call this entry point again in that
+ * process.  All calls share the array and it keeps the last call's contents
  * (the call itself clears what must start at zero), so calls that overlap
  * on the GPU -- other streams, threads or contexts on the same device --
  * race and must be serialised by the caller.  Returns after the count is on
@@ -375,7 +385,10 @@ int kx_mlp_adam(float* params, const float* grad, float* m, float* v, float lr, 
  * Errors: KX_ECAPACITY when n > KX_NOALLOC_MAX_TASKS (nothing is run) or
  * when the next frontier exceeds cap (the first cap tasks are written and
  * *n_next holds the full count); KX_ESTATE without tree or P norms;
- * KX_EINVAL for a bad level, pointer, size or tau. */
+ * KX_EINVAL for a bad level, pointer, size or tau, and when a task of
+ * `front` names a node id at or beyond the node count of level `level`
+ * (such tasks are skipped on the device without touching any table, the
+ * others are expanded and *n_next counts their children). */
 int kx_traverse_level_noalloc(kx_ctx* c, int32_t level, const uint16_t* front, int64_t n,
                               double tau, uint16_t* next, int64_t cap, int64_t* n_next);
 

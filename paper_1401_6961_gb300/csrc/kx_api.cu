@@ -163,7 +163,10 @@ int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int devi
         c->eri_bpsm[s] = 0;
         c->eri_variant[s] = 0;
     }
-    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) c->n_sm = 152;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->n_sm < 1) {
+        (void)cudaGetLastError();
+        c->n_sm = 0;
+    }
     std::vector<int32_t> tsys(c->n_shell);
     for (int y = 0; y < n_sys; ++y)
         for (int i = c->sys_shell[y]; i < c->sys_shell[y + 1]; ++i) tsys[i] = y;
@@ -184,6 +187,7 @@ int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int devi
         e = cudaMemcpyAsync(c->d_fseg, fseg.data(), sizeof(Seg) * n_sys, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) r = cuda_check(c, e, "kx_create");
+    if (r == KX_OK && c->n_sm < 1) r = set_err(c, KX_ECUDA, "multiprocessor count query failed");
     if (r == KX_OK) r = boys_table(c);
     if (r == KX_OK) r = order_atoms(c);
     if (r == KX_OK) r = function_positions(c);
@@ -493,7 +497,7 @@ int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter, int32_
         if (e == cudaSuccess && m > 0)
             e = cudaMemcpyAsync(d_out, c->d_keep, sizeof(Task) * m, cudaMemcpyDeviceToDevice, c->stream);
     } else if (e == cudaSuccess && c->keep_n > 0) {
-        unsigned grid = (unsigned)std::min<size_t>((c->keep_n + 255) / 256, 152 * 32);
+        unsigned grid = (unsigned)std::min<size_t>((c->keep_n + 255) / 256, (size_t)c->n_sm * 32);
         k_filter_work<<<grid, 256, 0, c->stream>>>(c->d_keep, (int64_t)c->keep_n, d_mark, d_out, d_cnt, cap);
         e = cudaGetLastError();
     }

@@ -292,18 +292,19 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
     return a;
 }
 
-static unsigned expand_grid(int64_t n) {
+// one warp per leaf quartet, at most 16 blocks per SM (a persistent grid)
+static unsigned expand_grid(const kx_ctx* c, int64_t n) {
     int64_t blocks = (n + EXP_WARPS - 1) / EXP_WARPS;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)c->n_sm * 16));
 }
 
-unsigned expand_blocks(int64_t n) { return expand_grid(n); }
+unsigned expand_blocks(const kx_ctx* c, int64_t n) { return expand_grid(c, n); }
 
 int expand_count(kx_ctx* c, const Task* leaves, int64_t n, double tau, double split, int mixed, int shell_screen,
                  int64_t* bin) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<false><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+    k_expand<false><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
                                                                        nullptr, nullptr);
     return KX_OK;
 }
@@ -312,7 +313,7 @@ int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
                  int64_t* bin_off, Quartet* rec) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<true><<<expand_grid(n), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
+    k_expand<true><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
                                                                       c->d_counters + CTR_END,
                                                                       c->d_counters + CTR_ERR);
     return KX_OK;
@@ -323,7 +324,7 @@ int expand_count_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* 
     if (cap <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, cap, tau, split, mixed, shell_screen);
     a.dn = dn;
-    k_expand<false><<<expand_grid(cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+    k_expand<false><<<expand_grid(c, cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
                                                                          nullptr, nullptr);
     c->launches++;
     return KX_OK;
@@ -334,7 +335,7 @@ int expand_write_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* 
     if (cap <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, cap, tau, split, mixed, shell_screen);
     a.dn = dn;
-    k_expand<true><<<expand_grid(cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
+    k_expand<true><<<expand_grid(c, cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
                                                                         c->d_counters + CTR_END,
                                                                         c->d_counters + CTR_ERR);
     c->launches++;

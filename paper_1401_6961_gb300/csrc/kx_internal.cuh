@@ -371,7 +371,7 @@ struct ClassCounts {
 // the number of kept quartets of every (stream, block) into bin[stream *
 // blocks + block] (blocks = expand_blocks(n)); after an exclusive scan of
 // bin, expand_write puts every record at its block's offset in its stream.
-unsigned expand_blocks(int64_t n_leaves);
+unsigned expand_blocks(const kx_ctx* c, int64_t n_leaves);
 int expand_count(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,
                  int mixed, int shell_screen, int64_t* bin);
 int expand_write(kx_ctx* c, const Task* leaves, int64_t n_leaves, double tau, double split,

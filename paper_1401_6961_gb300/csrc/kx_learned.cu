@@ -496,7 +496,7 @@ int kx_leaf_features(kx_ctx* c, float* feat, int64_t cap, int64_t* n) {
     KX_TRY(leaf_desc(c, &desc));
     const int D = c->depth, nl = c->levels[D].n;
     if (c->keep_n > 0) {
-        unsigned grid = (unsigned)std::min<size_t>((c->keep_n + 255) / 256, 152 * 32);
+        unsigned grid = (unsigned)std::min<size_t>((c->keep_n + 255) / 256, (size_t)c->n_sm * 32);
         k_features<<<grid, 256, 0, c->stream>>>(c->d_keep, (int64_t)c->keep_n, nl, c->d_nrm_s + c->pyr_off[D],
                                                c->d_nrm_p + c->pyr_off[D], desc, feat);
     }
@@ -526,7 +526,7 @@ int kx_cull_kept(kx_ctx* c, const float* pred, double tau, double log10_budget, 
     int* cnt = reinterpret_cast<int*>(c->d_scan + 2 * n);
     const double* S = c->d_nrm_s + c->pyr_off[D];
     const double* Pn = c->d_nrm_p + c->pyr_off[D];
-    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->n_sm * 32);
     KX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)nl * nl, c->stream));
     k_cull_count<<<grid, 256, 0, c->stream>>>(c->d_keep, n, nl, S, Pn, 10.0 * tau, cnt);
     k_cull_flags<<<grid, 256, 0, c->stream>>>(c->d_keep, n, nl, S, Pn, pred, 10.0 * tau, (float)log10_budget, cnt,
@@ -574,7 +574,11 @@ int kx_block_norms(kx_ctx* c, const double* K, int64_t ldk, const int32_t* leave
 int kx_mlp_infer_bf16(const float* params, const float* feat, int64_t n, float* pred, void* stream) {
     if (n < 0 || (n > 0 && (!params || !feat || !pred))) return KX_EINVAL;
     if (n == 0) return KX_OK;
-    unsigned grid = (unsigned)std::min<int64_t>((n + INF_T - 1) / INF_T, 152 * 8);
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || n_sm < 1)
+        return KX_ECUDA;
+    unsigned grid = (unsigned)std::min<int64_t>((n + INF_T - 1) / INF_T, (int64_t)n_sm * 8);
     k_mlp_infer<<<grid, INF_T, 0, (cudaStream_t)stream>>>(params, feat, n, pred);
     if (cudaGetLastError() != cudaSuccess) return KX_ECUDA;
     return KX_OK;

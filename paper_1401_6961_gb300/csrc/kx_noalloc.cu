@@ -10,22 +10,25 @@
 // Host code cannot use the array's name as a device address (it is a
 // host-side stand-in), so the first call on each device, with that device
 // current, asks the runtime for the address with cudaGetSymbolAddress and
-// caches it per device.
+// caches it per device.  The children's bounds and the compaction are the
+// device helpers of the traversal itself (kx_traverse_impl.cuh).
 #include <algorithm>
 #include <mutex>
 #include <string>
 
-#include "kx_internal.cuh"
+#include "kx_traverse_impl.cuh"
 
 namespace {
 
 using kx::Task;
+using kx::block_excl_scan64;
 
 constexpr int64_t NA_MAX = KX_NOALLOC_MAX_TASKS;
 constexpr int NA_T = 256, NA_I = 16, NA_TILE = NA_T * NA_I;
 constexpr int64_t NA_TILES = (NA_MAX + NA_TILE - 1) / NA_TILE;   // 64
 
-// scratch layout (bytes): counts | offsets | tile sums | tile offsets | total | masks
+// scratch layout (bytes): counts | offsets | tile sums | tile offsets |
+// total and bad-id count | masks
 constexpr size_t OFF_CNT = 0;
 constexpr size_t OFF_OFF = OFF_CNT + sizeof(int64_t) * NA_MAX;
 constexpr size_t OFF_TSUM = OFF_OFF + sizeof(int64_t) * NA_MAX;
@@ -57,53 +60,24 @@ int scratch_address(int device, unsigned char** out) {
     return KX_OK;
 }
 
-// children bounds of every task (same test as the traversal inside kx_exchange)
-__global__ void k_na_mask(const Task* __restrict__ front, int64_t n, const int32_t* __restrict__ child,
+// children bounds of every task (the test of the traversal inside
+// kx_exchange); a task naming a node id at or beyond the level's node count
+// n_level gets no children and is counted in *bad, and none of its ids is
+// used to index a table
+__global__ void k_na_mask(const Task* __restrict__ front, int64_t n, int n_level, const int32_t* __restrict__ child,
                           const int32_t* __restrict__ nchild, const double* __restrict__ S,
-                          const double* __restrict__ Pn, int nn, double tau, uint16_t* __restrict__ mask,
-                          int64_t* __restrict__ cnt) {
+                          const double* __restrict__ Pn, int nn, double tau, int sym, uint16_t* __restrict__ mask,
+                          int64_t* __restrict__ cnt, unsigned long long* __restrict__ bad) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const Task t = front[i];
-        const int ca = child[t.a], na = nchild[t.a], cb = child[t.b], nb = nchild[t.b];
-        const int cc = child[t.c], nc = nchild[t.c], cd = child[t.d], nd = nchild[t.d];
         unsigned m = 0;
-        for (int ia = 0; ia < na; ++ia)
-            for (int ib = 0; ib < nb; ++ib) {
-                const double sab = S[(int64_t)(ca + ia) * nn + (cb + ib)];
-                for (int id = 0; id < nd; ++id) {
-                    const double x = __dmul_rn(sab, Pn[(int64_t)(cb + ib) * nn + (cd + id)]);
-                    for (int ic = 0; ic < nc; ++ic)
-                        if (__dmul_rn(x, S[(int64_t)(cc + ic) * nn + (cd + id)]) > tau)
-                            m |= 1u << (((ia * 2 + ib) * 2 + ic) * 2 + id);
-                }
-            }
+        if (t.a < n_level && t.b < n_level && t.c < n_level && t.d < n_level)
+            m = kx::task_child_mask(t, child, nchild, S, Pn, 0, nn, tau, sym && t.a == t.c);
+        else
+            atomicAdd(bad, 1ull);
         mask[i] = (uint16_t)m;
         cnt[i] = __popc(m);
     }
-}
-
-__device__ int64_t na_block_scan(int64_t v, int64_t* sh, int64_t* total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int64_t x = v;
-    for (int d = 1; d < 32; d <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int64_t s = lane < nw ? sh[lane] : 0;
-        for (int d = 1; d < 32; d <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, s, d);
-            if (lane >= d) s += y;
-        }
-        sh[lane] = s;
-    }
-    __syncthreads();
-    int64_t ex = x - v + (w > 0 ? sh[w - 1] : 0);
-    *total = sh[nw - 1];
-    __syncthreads();
-    return ex;
 }
 
 // per-tile sums of the counts
@@ -115,7 +89,7 @@ __global__ void __launch_bounds__(NA_T) k_na_tiles(const int64_t* __restrict__ c
     for (int k = 0; k < NA_I; ++k)
         if (base + k < n) s += cnt[base + k];
     int64_t total;
-    na_block_scan(s, sh, &total);
+    block_excl_scan64(s, sh, &total);
     if (threadIdx.x == 0) tsum[blockIdx.x] = total;
 }
 
@@ -125,7 +99,7 @@ __global__ void __launch_bounds__(NA_T) k_na_tile_scan(const int64_t* __restrict
     __shared__ int64_t sh[32];
     const int64_t v = threadIdx.x < ntiles ? tsum[threadIdx.x] : 0;
     int64_t tot;
-    const int64_t ex = na_block_scan(v, sh, &tot);
+    const int64_t ex = block_excl_scan64(v, sh, &tot);
     if (threadIdx.x < ntiles) toff[threadIdx.x] = ex;
     if (threadIdx.x == 0) *total = tot;
 }
@@ -141,7 +115,7 @@ __global__ void __launch_bounds__(NA_T) k_na_offsets(const int64_t* __restrict__
         s += v[k];
     }
     int64_t total;
-    int64_t o = na_block_scan(s, sh, &total) + toff[blockIdx.x];
+    int64_t o = block_excl_scan64(s, sh, &total) + toff[blockIdx.x];
     for (int k = 0; k < NA_I; ++k) {
         if (base + k < n) off[base + k] = o;
         o += v[k];
@@ -149,22 +123,14 @@ __global__ void __launch_bounds__(NA_T) k_na_offsets(const int64_t* __restrict__
 }
 
 // children in the order (iA, iB, iC, iD); nothing is written at or past cap
+// (a task without children -- culled or with a bad id -- reads no table)
 __global__ void k_na_write(const Task* __restrict__ front, int64_t n, const uint16_t* __restrict__ mask,
                            const int64_t* __restrict__ off, const int32_t* __restrict__ child,
                            Task* __restrict__ out, int64_t cap) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned m = mask[i];
-        const Task t = front[i];
-        int64_t pos = off[i];
-        const int ca = child[t.a], cb = child[t.b], cc = child[t.c], cd = child[t.d];
-        while (m) {
-            const int bit = __ffs(m) - 1;
-            m &= m - 1;
-            if (pos < cap)
-                out[pos] = Task{(uint16_t)(ca + ((bit >> 3) & 1)), (uint16_t)(cb + ((bit >> 2) & 1)),
-                                (uint16_t)(cc + ((bit >> 1) & 1)), (uint16_t)(cd + (bit & 1))};
-            ++pos;
-        }
+        const unsigned m = mask[i];
+        if (!m) continue;
+        kx::write_children(front[i], m, child, out, off[i], cap);
     }
 }
 
@@ -208,29 +174,34 @@ extern "C" int kx_traverse_level_noalloc(kx_ctx* c, int32_t level, const uint16_
     int64_t* total = reinterpret_cast<int64_t*>(base + OFF_TOTAL);
     uint16_t* mask = reinterpret_cast<uint16_t*>(base + OFF_MASK);
     cudaStream_t st = c->stream;
-    // the grand total starts at zero for an empty frontier
-    cudaError_t e = cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+    unsigned long long* bad = reinterpret_cast<unsigned long long*>(base + OFF_TOTAL + 8);
+    // the grand total (for an empty frontier) and the bad-id count start at zero
+    cudaError_t e = cudaMemsetAsync(total, 0, 16, st);
     if (e == cudaSuccess && n > 0) {
         const int nn = c->levels[level + 1].n;
+        const int n_level = c->levels[level].n;
         const int32_t* child = c->d_node_child + c->levels[level].off;
         const int32_t* nchild = c->d_node_nchild + c->levels[level].off;
         const double* S = c->d_nrm_s + c->pyr_off[level + 1];
         const double* Pn = c->d_nrm_p + c->pyr_off[level + 1];
         const Task* fr = reinterpret_cast<const Task*>(front);
-        const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+        const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->n_sm * 16);
         const int ntiles = (int)((n + NA_TILE - 1) / NA_TILE);
-        k_na_mask<<<g1, 256, 0, st>>>(fr, n, child, nchild, S, Pn, nn, tau, mask, cnt);
+        k_na_mask<<<g1, 256, 0, st>>>(fr, n, n_level, child, nchild, S, Pn, nn, tau, c->build_sym, mask, cnt, bad);
         k_na_tiles<<<ntiles, NA_T, 0, st>>>(cnt, n, tsum);
         k_na_tile_scan<<<1, NA_T, 0, st>>>(tsum, ntiles, toff, total);
         k_na_offsets<<<ntiles, NA_T, 0, st>>>(cnt, n, toff, off);
         k_na_write<<<g1, 256, 0, st>>>(fr, n, mask, off, child, reinterpret_cast<Task*>(next), cap);
         e = cudaGetLastError();
     }
-    int64_t h = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, total, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    int64_t h[2] = {0, 0};   // total, bad ids
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, total, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return kx::cuda_check(c, e, "kx_traverse_level_noalloc");
-    *n_next = h;
-    if (h > cap) return kx::set_err(c, KX_ECAPACITY, "next frontier larger than cap");
+    *n_next = h[0];
+    if (h[1] != 0)
+        return kx::set_err(c, KX_EINVAL, std::to_string(h[1]) + " tasks name node ids outside level " +
+                                             std::to_string(level));
+    if (h[0] > cap) return kx::set_err(c, KX_ECAPACITY, "next frontier larger than cap");
     return KX_OK;
 }

@@ -17,7 +17,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "kx_internal.cuh"
+#include "kx_traverse_impl.cuh"
 
 namespace kx {
 
@@ -28,32 +28,6 @@ namespace kx {
 constexpr int SCAN_T = 256;
 constexpr int SCAN_I = 16;
 constexpr int SCAN_TILE = SCAN_T * SCAN_I;
-
-__device__ int64_t block_excl_scan64(int64_t v, int64_t* sh, int64_t* total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int64_t x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int64_t s = lane < nw ? sh[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, s, d);
-            if (lane >= d) s += y;
-        }
-        sh[lane] = s;
-    }
-    __syncthreads();
-    int64_t ex = x - v + (w > 0 ? sh[w - 1] : 0);
-    *total = sh[nw - 1];
-    __syncthreads();
-    return ex;
-}
 
 // n = *dn when dn is given (the grid then covers a capacity >= *dn)
 __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int64_t* __restrict__ in, int64_t n,
@@ -164,28 +138,9 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
     if (dn) n = min(n, *dn);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const Task t = front[i];
-        // symmetric build: only K blocks (A,C) with A <= C; a node left of
-        // another has all its children left of the other's
-        const bool diag = sym && t.a == t.c;
+        // symmetric build: only K blocks (A,C) with A <= C
         const Seg g = lseg_next[node_sys[t.a]];
-        const int64_t t0 = g.t0();
-        const int nn = g.n;
-        const int ca = child[t.a], na = nchild[t.a];
-        const int cb = child[t.b], nb = nchild[t.b];
-        const int cc = child[t.c], nc = nchild[t.c];
-        const int cd = child[t.d], nd = nchild[t.d];
-        unsigned m = 0;
-        for (int ia = 0; ia < na; ++ia)
-            for (int ib = 0; ib < nb; ++ib) {
-                const double sab = S[t0 + (int64_t)(ca + ia) * nn + (cb + ib)];
-                for (int id = 0; id < nd; ++id) {
-                    const double x = __dmul_rn(sab, Pn[t0 + (int64_t)(cb + ib) * nn + (cd + id)]);
-                    for (int ic = diag ? ia : 0; ic < nc; ++ic) {
-                        const double beta = __dmul_rn(x, S[t0 + (int64_t)(cc + ic) * nn + (cd + id)]);
-                        if (beta > tau) m |= 1u << (((ia * 2 + ib) * 2 + ic) * 2 + id);
-                    }
-                }
-            }
+        const unsigned m = task_child_mask(t, child, nchild, S, Pn, g.t0(), g.n, tau, sym && t.a == t.c);
         mask[i] = (uint16_t)m;
         cnt[i] = __popc(m);
     }
@@ -204,17 +159,9 @@ __global__ void k_expand_write(const Task* __restrict__ front, int64_t p0, int64
     }
     for (int64_t i = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p1;
          i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned m = mask[i];
+        const unsigned m = mask[i];
         if (!m) continue;
-        const Task t = front[i];
-        int64_t pos = off[i] - obase;
-        const int ca = child[t.a], cb = child[t.b], cc = child[t.c], cd = child[t.d];
-        while (m) {
-            const int bit = __ffs(m) - 1;
-            m &= m - 1;
-            out[pos++] = Task{(uint16_t)(ca + ((bit >> 3) & 1)), (uint16_t)(cb + ((bit >> 2) & 1)),
-                              (uint16_t)(cc + ((bit >> 1) & 1)), (uint16_t)(cd + (bit & 1))};
-        }
+        write_children(front[i], m, child, out, off[i] - obase, INT64_MAX);
     }
 }
 
@@ -409,7 +356,7 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     const int mixed = r.o->precision == KX_MIXED;
     const double split = mixed ? r.o->split_threshold : 0.0;
     r.tm->mark(ST_EXPAND);
-    const unsigned nb = expand_blocks(n);
+    const unsigned nb = expand_blocks(c, n);
     const int64_t nbin = (int64_t)2 * NCLASS * nb;
     KX_TRY(grow(c, &c->d_bin, &c->bin_cap, (size_t)(2 * nbin)));
     int64_t* bin = c->d_bin;
@@ -616,7 +563,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
             KX_TRY(grow(c, &c->d_scan, &c->scan_cap, (size_t)2 * nfront));
             int64_t* cnt = c->d_scan;
             int64_t* off = c->d_scan + nfront;
-            unsigned g = (unsigned)std::min<int64_t>((nfront + 255) / 256, 152 * 64);
+            unsigned g = (unsigned)std::min<int64_t>((nfront + 255) / 256, (int64_t)c->n_sm * 64);
             k_expand_mask<<<g, 256, 0, c->stream>>>(c->d_front[cur], nfront, child, nchild, nsys, lnext, S, Pn,
                                                     o->tau, c->d_mask, cnt, nullptr, o->symmetric);
             c->launches++;
@@ -659,7 +606,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
                 KX_CUDA(c, cudaStreamSynchronize(c->stream));
                 if (p1 >= nfront) o1 = total;
                 tm.mark(ST_EXPAND);
-                unsigned g2 = (unsigned)std::min<int64_t>((p1 - p0 + 255) / 256, 152 * 64);
+                unsigned g2 = (unsigned)std::min<int64_t>((p1 - p0 + 255) / 256, (int64_t)c->n_sm * 64);
                 k_expand_write<<<g2, 256, 0, c->stream>>>(c->d_front[cur], p0, p1, c->d_mask, off, o0, child,
                                                           c->d_front[1 - cur], nullptr);
                 c->launches++;
@@ -828,7 +775,7 @@ int chunk_dev(kx_ctx* c, const kx_opts* o, const GraphWords& W, const GraphCaps&
               int64_t leaf_cap, const int64_t* dn, const double* P, double* K) {
     const int mixed = o->precision == KX_MIXED;
     const double split = mixed ? o->split_threshold : 0.0;
-    const unsigned nb = expand_blocks(leaf_cap);
+    const unsigned nb = expand_blocks(c, leaf_cap);
     const int64_t nbin = (int64_t)2 * NCLASS * nb;
     int64_t* bin = c->d_bin;
     int64_t* binoff = c->d_bin + nbin;
@@ -924,7 +871,7 @@ namespace {
 int capture_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, const GraphCaps& cap) {
     const int D = c->depth, ny = c->n_sys;
     GraphWords W{D, (int)cap.nch};
-    const unsigned nb = expand_blocks(cap.lq + 16);
+    const unsigned nb = expand_blocks(c, cap.lq + 16);
     const int64_t nbin = (int64_t)2 * NCLASS * nb;
     const int64_t fcap = std::max<int64_t>({cap.fcap, cap.lq + 16, (int64_t)ny + 16});
     KX_TRY(grow(c, &c->d_front[0], &c->front_cap[0], (size_t)fcap));

@@ -4,7 +4,8 @@ It serves callers that cannot let a library allocate device memory (all
 memory handed to their own allocator up front, or no allocation after
 start-up).  Its output must equal the existing entry point's: walking it
 level by level from the root task gives exactly the leaf-quartet worklist
-that kx_exchange keeps (kx_get_worklist) for the same tau.  Worklists are
+that kx_exchange keeps (kx_get_worklist) for the same tau, in plain and in
+symmetric builds (there only the K blocks A <= C).  Worklists are
 integers, so the comparison is exact.  Two calls in a row check that the
 shared scratch array carries nothing over.  This file sorts last so that a
 run stopping at the first failure has run every other test first.
@@ -54,17 +55,38 @@ def _systems():
     return [(w4, P4, 1e-10, 4), (s3, wl.density(s3, 3003), 1e-10, 10), (w4, P4, 1e-3, 4)]
 
 
+@pytest.mark.parametrize("symmetric", [0, 1])
 @pytest.mark.parametrize("case", [0, 1, 2])
-def test_noalloc_level_walk_matches_kx_exchange(kx, case):
+def test_noalloc_level_walk_matches_kx_exchange(kx, case, symmetric):
     import torch
     sys_, P, tau, leaf_max = _systems()[case]
     ex = kx.Exchange(sys_, leaf_max=leaf_max)
-    ex(torch.from_numpy(P).cuda(), tau=tau, keep_worklist=1)
+    ex(torch.from_numpy(P).cuda(), tau=tau, keep_worklist=1, symmetric=symmetric)
     ref = _sorted(ex.worklist())
     assert len(ref) > 0
+    if symmetric:
+        assert (ref[:, 0] <= ref[:, 2]).all()
     for _ in range(2):
         got = _sorted(_walk(kx, ex, tau))
         assert got.shape == ref.shape and np.array_equal(got, ref)
+    ex.close()
+
+
+def test_noalloc_rejects_node_ids_outside_the_level(kx):
+    import torch
+    sys_, P = wl.workload("water4")
+    ex = kx.Exchange(sys_)
+    ex(torch.from_numpy(P).cuda(), tau=1e-10)
+    # level 0 holds one node (the root): id 3 is outside it; the kernel skips
+    # that task without reading any table and the call reports KX_EINVAL
+    front = torch.tensor([[0, 0, 0, 0], [0, 3, 0, 0]], dtype=torch.int16, device="cuda")
+    nxt = torch.empty((64, 4), dtype=torch.int16, device="cuda")
+    with pytest.raises(kx.KxError) as e:
+        kx.kx_traverse_level_noalloc(ex.ctx, 0, front.data_ptr(), 2, 1e-10, nxt.data_ptr(), 64)
+    assert e.value.code == kx.KX_EINVAL
+    # the valid task alone still expands as before
+    n = kx.kx_traverse_level_noalloc(ex.ctx, 0, front.data_ptr(), 1, 1e-10, nxt.data_ptr(), 64)
+    assert 0 < n <= 16
     ex.close()
 
 
