@@ -77,7 +77,14 @@ typedef struct {
     int32_t symmetric;           /* 1: P is symmetric, so K = K^T: only the K blocks (A,C)
                                     with A <= C (tree order; shells a <= c inside a
                                     diagonal block) are built and the rest mirrored */
+    int32_t row_leaf_lo;         /* K row-block shard: only tasks whose row block A lies in */
+    int32_t row_leaf_hi;         /* the leaves [row_leaf_lo, row_leaf_hi) are traversed and
+                                    evaluated (0, 0 = every leaf); see kx_row_work */
     int32_t reserved;            /* 0 */
+    double split_budget;         /* KX_MIXED, > 0: split_threshold is ignored and the split is
+                                    chosen per build from the FP32 error model so that the
+                                    estimated max|dK| of the FP32 quartets stays within this
+                                    budget (kx_stats.split_used, fp32_err_estimate) */
 } kx_opts;
 
 /* Counters and stage times of the last build. */
@@ -99,6 +106,13 @@ typedef struct {
     double ms_eri;               /* ERI evaluation + contraction */
     double ms_eri_kernel_max;    /* longest single ERI class launch */
     double ms_total;
+    double split_used;           /* KX_MIXED: the split threshold of the build */
+    double fp32_err_bound;       /* KX_MIXED: c_max eps32 * (largest sum over one K shell block
+                                    of the FP32 quartets' bounds beta), a bound on max|dK|
+                                    from FP32 rounding under the per-quartet error model */
+    double fp32_err_estimate;    /* KX_MIXED: c_rms eps32 * (largest root-sum-square over one
+                                    K shell block of the FP32 quartets' beta), the expected
+                                    size of that error for independent roundings */
 } kx_stats;
 
 /* Fills the defaults: tau = 1e-10, split 1e-5, FP64, shell screen on,
@@ -151,6 +165,28 @@ int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts
  * P: DEVICE, as for kx_exchange (ldp >= n_fn), or packed per system with
  * ldp = 0 on a batch context.  st is required.  Synchronous. */
 int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats* st);
+
+/* K row-block shards (several GPUs).  The leaf quartets are independent,
+ * so the build splits by the row block A of K (mu in A): a build with
+ * kx_opts.row_leaf_lo/hi traverses (Eqs. 7-8) and evaluates only the tasks
+ * whose A lies in those leaves, and writes only their contributions (its
+ * rows, and in a symmetric build the mirrored columns of those rows); K is
+ * zero elsewhere.  Summing the K of the shards [b_0, b_1), [b_1, b_2), ...
+ * gives the K of the whole build (every entry comes from exactly one
+ * shard), and the union of their worklists is its worklist.
+ *
+ * kx_row_work: work[leaf] (host array of the leaf count of kx_get_leaves)
+ * = algorithmic FLOPs of the ERI stage of the tasks with that row leaf, in
+ * the build with these options (its traversal and count pass, no K);
+ * P as for kx_count.  Synchronous. */
+int kx_row_work(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* work);
+
+/* Contiguous shards of balanced work: bounds[0] = 0 < bounds[1] < ... <
+ * bounds[n_shards] = n_leaf, each boundary the leaf boundary whose prefix
+ * sum of work is nearest j/n_shards of the total (equal leaf counts when
+ * all work is zero).  Host only (no device, no context); KX_EINVAL unless
+ * 1 <= n_shards <= n_leaf and every work[i] is finite and >= 0. */
+int kx_shard_bounds(const double* work, int32_t n_leaf, int32_t n_shards, int32_t* bounds);
 
 /* ------------------------------------------------------------------------
  * Batches of independent systems (a growth direction beyond the paper: many
@@ -263,10 +299,13 @@ int kx_get_norms(kx_ctx* c, double* s2, double* pq);
  * launches = kernel launches.  Host arrays of 162 entries (any may be NULL). */
 int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32_t* launches);
 
-/* Throughput probe of the plain FMA pipe on `device`: a kernel of
- * independent fused multiply-add chains, timed with CUDA events; precision
- * KX_FP64 or KX_MIXED (= FP32).  *gflops = measured GFLOP/s (2 per FMA).
- * Not part of the exchange build; used to state roofline fractions. */
+/* Throughput probe on `device`, timed with CUDA events (best of five after
+ * a warm-up launch).  precision KX_FP64 or KX_MIXED (= FP32): independent
+ * fused multiply-add chains on the plain FMA pipe; KX_PROBE_FP64_MMA: FP64
+ * tensor-core (DMMA, mma.sync m8n8k4) chains.  *gflops = measured GFLOP/s
+ * (2 per multiply-add).  Not part of the exchange build; used to state
+ * roofline fractions and to decide where tensor cores would pay. */
+#define KX_PROBE_FP64_MMA 2
 int kx_peak_probe(int device, int precision, double* gflops);
 
 /* ------------------------------------------------------------------------

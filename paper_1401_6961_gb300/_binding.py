@@ -27,11 +27,12 @@ EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", 
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
            "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
            "kx_block_norms", "kx_mlp_infer_bf16", "kx_mlp_loss_grad", "kx_mlp_adam",
-           "kx_last_error", "kx_destroy"]
+           "kx_row_work", "kx_shard_bounds", "kx_last_error", "kx_destroy"]
 KX_NFEAT = 10
 KX_MLP_HIDDEN = 64
 KX_MLP_NPARAM = 9109
 KX_NOALLOC_MAX_TASKS = 1 << 18
+KX_PROBE_FP64_MMA = 2
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -47,7 +48,9 @@ class kx_opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("split_threshold", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("shell_screen", ctypes.c_int32),
                 ("keep_worklist", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("chunk_records", ctypes.c_int64), ("symmetric", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("chunk_records", ctypes.c_int64), ("symmetric", ctypes.c_int32),
+                ("row_leaf_lo", ctypes.c_int32), ("row_leaf_hi", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("split_budget", ctypes.c_double)]
 
 
 class kx_stats(ctypes.Structure):
@@ -58,7 +61,8 @@ class kx_stats(ctypes.Structure):
                 ("flops_fp32", ctypes.c_double), ("ms_norms", ctypes.c_double),
                 ("ms_traverse", ctypes.c_double), ("ms_expand", ctypes.c_double),
                 ("ms_eri", ctypes.c_double), ("ms_eri_kernel_max", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("split_used", ctypes.c_double),
+                ("fp32_err_bound", ctypes.c_double), ("fp32_err_estimate", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "n_tasks")}
@@ -117,6 +121,8 @@ def load() -> ctypes.CDLL:
     L.kx_get_norms.argtypes = [vp, _f64p, _f64p]
     L.kx_get_profile.argtypes = [vp, _f64p, _i64p, _f64p, _i32p]
     L.kx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _f64p]
+    L.kx_row_work.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), _f64p]
+    L.kx_shard_bounds.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int32, _i32p]
     L.kx_traverse_level_noalloc.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_double, vp,
                                             ctypes.c_int64, _i64p]
     L.kx_traverse.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), _i64p]
@@ -342,12 +348,39 @@ def kx_get_profile(ctx) -> dict:
 
 
 def kx_peak_probe(device: int = 0, precision: int = KX_FP64) -> float:
-    """Measured FMA-pipe throughput in GFLOP/s (FP64 or, with KX_MIXED, FP32)."""
+    """Measured throughput in GFLOP/s: the FMA pipe (FP64 or, with KX_MIXED,
+    FP32) or, with KX_PROBE_FP64_MMA, the FP64 tensor cores (DMMA)."""
     g = ctypes.c_double()
     r = load().kx_peak_probe(int(device), int(precision), ctypes.byref(g))
     if r != KX_OK:
         raise KxError(r, "kx_peak_probe failed")
     return float(g.value)
+
+
+def kx_row_work(ctx, P_ptr: int, ldp: int, opts: kx_opts) -> np.ndarray:
+    """Algorithmic FLOPs of the ERI stage per row leaf A (leaf ordinal) of
+    the build with these options, from its traversal and count pass."""
+    _, n_leaf = _n_leaves(ctx)
+    w = np.zeros(n_leaf)
+    _check(ctx, load().kx_row_work(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts), _p(w, _f64p)))
+    return w
+
+
+def _n_leaves(ctx):
+    nl, dep = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, load().kx_get_leaves(ctx, None, None, 0, ctypes.byref(nl), ctypes.byref(dep)))
+    return int(dep.value), int(nl.value)
+
+
+def kx_shard_bounds(work, n_shards: int) -> np.ndarray:
+    """Leaf boundaries [n_shards + 1] of contiguous row-block shards of
+    balanced work (host computation, no device)."""
+    w = np.ascontiguousarray(work, dtype=np.float64)
+    b = np.zeros(int(n_shards) + 1, dtype=np.int32)
+    r = load().kx_shard_bounds(_p(w, _f64p), int(w.shape[0]), int(n_shards), _p(b, _i32p))
+    if r != KX_OK:
+        raise KxError(r, "kx_shard_bounds failed")
+    return b
 
 
 def kx_traverse_level_noalloc(ctx, level: int, front_ptr: int, n: int, tau: float, next_ptr: int,
@@ -504,6 +537,12 @@ class Exchange:
     def replay(self):
         self.stats = kx_graph_launch(self.ctx)
         return self._graph_bufs[1]
+
+    def row_work(self, P, **opts) -> np.ndarray:
+        """Work (algorithmic FLOPs) per row leaf of the build ``self(P, **opts)``."""
+        import torch
+        assert P.is_cuda and P.dtype == torch.float64 and P.stride(1) == 1 and P.shape == (self.n_fn, self.n_fn)
+        return kx_row_work(self.ctx, P.data_ptr(), P.stride(0), kx_default_opts(**opts))
 
     def worklist(self, a_filter=None) -> np.ndarray:
         return kx_get_worklist(self.ctx, a_filter)

@@ -347,6 +347,56 @@ int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats
     return drive(c, RUN_COUNT, P, ldp, o, nullptr, 0, st, nullptr, 0);
 }
 
+int kx_row_work(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* work) {
+    KX_TRY(check_ctx(c));
+    if (!work) return set_err(c, KX_EINVAL, "null argument");
+    if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
+    const int nl = c->levels[c->depth].n;
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    if (!c->d_sflops) {
+        float h[2 * NCLASS];
+        for (int s = 0; s < 2 * NCLASS; ++s) h[s] = (float)class_flops(s % NCLASS);
+        KX_CUDA(c, cudaMalloc(&c->d_sflops, sizeof(h)));
+        KX_CUDA(c, cudaMemcpy(c->d_sflops, h, sizeof(h), cudaMemcpyHostToDevice));
+    }
+    KX_TRY(grow(c, &c->d_work, &c->work_cap, (size_t)nl));
+    KX_CUDA(c, cudaMemsetAsync(c->d_work, 0, sizeof(double) * nl, c->stream));
+    kx_stats st;
+    c->work_acc = c->d_work;
+    const int r = kx_count(c, P, ldp, o, &st);
+    c->work_acc = nullptr;
+    if (r != KX_OK) return r;
+    KX_CUDA(c, cudaMemcpyAsync(work, c->d_work, sizeof(double) * nl, cudaMemcpyDeviceToHost, c->stream));
+    KX_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KX_OK;
+}
+
+int kx_shard_bounds(const double* work, int32_t n_leaf, int32_t n_shards, int32_t* bounds) {
+    if (!work || !bounds || n_leaf < 1 || n_shards < 1 || n_shards > n_leaf) return KX_EINVAL;
+    double total = 0.0;
+    for (int32_t i = 0; i < n_leaf; ++i) {
+        if (!(work[i] >= 0.0) || !std::isfinite(work[i])) return KX_EINVAL;
+        total += work[i];
+    }
+    std::vector<double> pre(n_leaf + 1, 0.0);   // pre[i] = work of leaves [0, i)
+    for (int32_t i = 0; i < n_leaf; ++i) pre[i + 1] = pre[i] + (total > 0.0 ? work[i] : 1.0);
+    const double all = pre[n_leaf];
+    bounds[0] = 0;
+    bounds[n_shards] = n_leaf;
+    for (int32_t j = 1; j < n_shards; ++j) {
+        // the leaf boundary whose prefix is nearest j/n of the total
+        const double target = all * (double)j / (double)n_shards;
+        int32_t i = (int32_t)(std::lower_bound(pre.begin(), pre.end(), target) - pre.begin());
+        if (i > 0 && target - pre[i - 1] <= pre[std::min(i, n_leaf)] - target) --i;
+        // every shard keeps at least one leaf
+        i = std::max(i, bounds[j - 1] + 1);
+        i = std::min(i, n_leaf - (n_shards - j));
+        bounds[j] = i;
+    }
+    return KX_OK;
+}
+
 int kx_exchange_batch(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st) {
     KX_TRY(check_ctx(c));
     return exchange_impl(c, P, 0, o, K, 0, st);
@@ -561,7 +611,8 @@ int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32
 }
 
 int kx_peak_probe(int device, int precision, double* gflops) {
-    if (!gflops || (precision != KX_FP64 && precision != KX_MIXED)) return KX_EINVAL;
+    if (!gflops || (precision != KX_FP64 && precision != KX_MIXED && precision != KX_PROBE_FP64_MMA))
+        return KX_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         (void)cudaGetLastError();

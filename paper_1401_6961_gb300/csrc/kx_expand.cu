@@ -46,6 +46,11 @@ struct ExpandArgs {
     float ltau, lsplit;
     int mixed, screen;
     int sym;                 // symmetric build: inside a diagonal block (A == C) only a <= c
+    // count pass only, may be null: work[A] += the algorithmic FLOPs of the
+    // kept shell quartets of every leaf quartet with row leaf A (sflops[s]
+    // = FLOPs of one quartet of stream s)
+    double* work;
+    const float* sflops;
 };
 
 __device__ __forceinline__ bool above(float x, float lthr, double thr, const double* __restrict__ snorm,
@@ -105,9 +110,13 @@ __device__ __forceinline__ int decide(const ExpandArgs& p, float x, float sab, f
 template <bool WRITE>
 __device__ __forceinline__ void emit(int stream, int32_t pab, int32_t pcd, int lane, unsigned int* scount,
                                      Quartet* __restrict__ rec, const unsigned long long* __restrict__ end,
-                                     unsigned long long* __restrict__ err) {
+                                     unsigned long long* __restrict__ err, const float* __restrict__ sflops,
+                                     float& wsum) {
     if (!WRITE) {
-        if (stream >= 0) atomicAdd(&scount[stream], 1u);
+        if (stream >= 0) {
+            atomicAdd(&scount[stream], 1u);
+            if (sflops) wsum += __ldg(sflops + stream);
+        }
         return;
     }
     const unsigned keepmask = __ballot_sync(0xffffffffu, stream >= 0);
@@ -144,6 +153,7 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
     const int64_t nq = p.dn ? min(p.n, *p.dn) : p.n;
     for (int64_t q = warp; q < nq; q += nwarp) {
         const Task t = p.leaves[q];
+        float wsum = 0.f;   // FLOPs of this lane's kept candidates (row-work counts only)
         const int a0 = p.llo[t.a], na = p.lhi[t.a] - a0;
         const int b0 = p.llo[t.b], nb = p.lhi[t.b] - b0;
         const int c0 = p.llo[t.c], nc = p.lhi[t.c] - c0;
@@ -231,7 +241,7 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                         stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns,
                                                pab, pcd);
                 }
-                emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
+                emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err, p.sflops, wsum);
             }
         } else {
             // very large leaves: read the tables from global memory
@@ -251,8 +261,12 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
                     if (!(diag && a > c)) stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, t0, ns, pab, pcd);
                 }
-                emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err);
+                emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err, p.sflops, wsum);
             }
+        }
+        if (!WRITE && p.work) {
+            for (int d = 16; d > 0; d >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, d);
+            if (lane == 0 && wsum > 0.f) atomicAdd(p.work + t.a, (double)wsum);
         }
     }
     if (!WRITE) {
@@ -289,6 +303,8 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
     a.mixed = mixed;
     a.screen = screen;
     a.sym = sym;
+    a.work = c->work_acc;
+    a.sflops = c->d_sflops;
     return a;
 }
 

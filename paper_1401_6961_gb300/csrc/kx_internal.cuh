@@ -300,6 +300,12 @@ struct kx_ctx {
     double prof_flops[2 * kx::NCLASS] = {};
     int32_t prof_launches[2 * kx::NCLASS] = {};
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+    // per-row-leaf work of a kx_row_work count (null otherwise) and the
+    // FLOPs of one quartet of every stream
+    double* work_acc = nullptr;
+    double* d_work = nullptr;
+    size_t work_cap = 0;
+    float* d_sflops = nullptr;
 };
 
 namespace kx {

@@ -72,7 +72,7 @@ __global__ void k_na_mask(const Task* __restrict__ front, int64_t n, int n_level
         const Task t = front[i];
         unsigned m = 0;
         if (t.a < n_level && t.b < n_level && t.c < n_level && t.d < n_level)
-            m = kx::task_child_mask(t, child, nchild, S, Pn, 0, nn, tau, sym && t.a == t.c);
+            m = kx::task_child_mask(t, child, nchild, S, Pn, 0, nn, tau, sym && t.a == t.c, kx::RowRange{nullptr, nullptr, 0, 0});
         else
             atomicAdd(bad, 1ull);
         mask[i] = (uint16_t)m;

@@ -985,6 +985,28 @@ __global__ void __launch_bounds__(256) k_fma_probe(R* __restrict__ out, int iter
     out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
 }
 
+// FP64 tensor-core (DMMA) chains: mma.sync m8n8k4 with FP64 operands, four
+// independent accumulator tiles per warp; each instruction is 8*8*4
+// multiply-adds of the warp.  a and b stay fixed, so the accumulators grow
+// linearly and stay finite.
+__global__ void __launch_bounds__(256) k_dmma_probe(double* __restrict__ out, int iters, double a, double b) {
+    double c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c[k] = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                         : "+d"(c[2 * k]), "+d"(c[2 * k + 1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += c[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 int peak_probe(int device, int precision, double* gflops) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
@@ -992,7 +1014,7 @@ int peak_probe(int device, int precision, double* gflops) {
         return KX_ECUDA;
     }
     const int blocks = prop.multiProcessorCount * 8, threads = 256;
-    const int iters = precision == KX_FP64 ? 1 << 12 : 1 << 17;
+    const int iters = precision == KX_FP64 ? 1 << 12 : (precision == KX_PROBE_FP64_MMA ? 1 << 10 : 1 << 17);
     void* out = nullptr;
     if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1006,13 +1028,18 @@ int peak_probe(int device, int precision, double* gflops) {
         cudaEventRecord(e0);
         if (precision == KX_FP64)
             k_fma_probe<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-6);
+        else if (precision == KX_PROBE_FP64_MMA)
+            k_dmma_probe<<<blocks, threads>>>((double*)out, iters, 1e-3, 1e-3);
         else
             k_fma_probe<float><<<blocks, threads>>>((float*)out, iters, 0.9999f, 1e-4f);
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+        // FMA probes: 8 chains of one FMA per thread; DMMA: 4 instructions of
+        // 256 multiply-adds per warp, i.e. 32 per thread
+        const double per_thread = precision == KX_PROBE_FP64_MMA ? 4.0 * 256.0 / 32.0 : 8.0;
+        const double flops = 2.0 * per_thread * iters * (double)blocks * threads;
         if (rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e9);
     }
     cudaError_t e = cudaGetLastError();

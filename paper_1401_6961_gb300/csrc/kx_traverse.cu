@@ -134,13 +134,14 @@ __global__ void k_expand_mask(const Task* __restrict__ front, int64_t n, const i
                               const int32_t* __restrict__ nchild, const int32_t* __restrict__ node_sys,
                               const Seg* __restrict__ lseg_next, const double* __restrict__ S,
                               const double* __restrict__ Pn, double tau, uint16_t* __restrict__ mask,
-                              int64_t* __restrict__ cnt, const int64_t* __restrict__ dn, int sym) {
+                              int64_t* __restrict__ cnt, const int64_t* __restrict__ dn, int sym,
+                              const RowRange rows) {
     if (dn) n = min(n, *dn);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const Task t = front[i];
         // symmetric build: only K blocks (A,C) with A <= C
         const Seg g = lseg_next[node_sys[t.a]];
-        const unsigned m = task_child_mask(t, child, nchild, S, Pn, g.t0(), g.n, tau, sym && t.a == t.c);
+        const unsigned m = task_child_mask(t, child, nchild, S, Pn, g.t0(), g.n, tau, sym && t.a == t.c, rows);
         mask[i] = (uint16_t)m;
         cnt[i] = __popc(m);
     }
@@ -169,9 +170,9 @@ __global__ void k_expand_write(const Task* __restrict__ front, int64_t p0, int64
 // bound exceeds tau, in system order (one thread: only for tiny systems)
 __global__ void k_root_only(const Seg* __restrict__ lseg0, int nsys, const double* __restrict__ S,
                             const double* __restrict__ Pn, double tau, Task* __restrict__ out,
-                            int64_t* __restrict__ n_out) {
+                            int64_t* __restrict__ n_out, int leaf0, int leaf1) {
     int64_t k = 0;
-    for (int y = 0; y < nsys; ++y) {
+    for (int y = leaf0; y < leaf1; ++y) {
         const int64_t i = lseg0[y].off;   // the block of a one-node level: (y, y)
         const double beta = __dmul_rn(__dmul_rn(S[i], Pn[i]), S[i]);
         if (beta > tau) out[k++] = Task{(uint16_t)y, (uint16_t)y, (uint16_t)y, (uint16_t)y};
@@ -454,9 +455,38 @@ int keep_leaves(kx_ctx* c, const Task* leaves, int64_t n) {
 
 }  // namespace
 
+// The leaves [*l0, *l1) of the build's K row-block shard (every leaf when
+// the options name none); KX_EINVAL for a range outside the leaves.
+int row_leaves(kx_ctx* c, const kx_opts* o, int* l0, int* l1) {
+    const int nl = c->levels[c->depth].n;
+    if (o->row_leaf_lo == 0 && o->row_leaf_hi == 0) {
+        *l0 = 0;
+        *l1 = nl;
+        return KX_OK;
+    }
+    if (o->row_leaf_lo < 0 || o->row_leaf_lo >= o->row_leaf_hi || o->row_leaf_hi > nl)
+        return set_err(c, KX_EINVAL, "row_leaf_lo/row_leaf_hi must satisfy 0 <= lo < hi <= " + std::to_string(nl));
+    *l0 = o->row_leaf_lo;
+    *l1 = o->row_leaf_hi;
+    return KX_OK;
+}
+
+// The shard's row filter for the children at `level` (no filter when the
+// shard is every leaf)
+RowRange row_range(const kx_ctx* c, const kx_opts* o, int level) {
+    const int nl = c->levels[c->depth].n;
+    if ((o->row_leaf_lo == 0 && o->row_leaf_hi == 0) || (o->row_leaf_lo == 0 && o->row_leaf_hi == nl))
+        return RowRange{nullptr, nullptr, 0, 0};
+    const int lv = c->levels[c->depth].off;
+    return RowRange{c->d_node_lo + c->levels[level].off, c->d_node_hi + c->levels[level].off,
+                    c->node_lo[lv + o->row_leaf_lo], c->node_hi[lv + o->row_leaf_hi - 1]};
+}
+
 int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, double* K, int64_t ldk,
           kx_stats* st, const Task* list, int64_t nlist) {
     const int D = c->depth;
+    int rl0 = 0, rl1 = 0;
+    KX_TRY(row_leaves(c, o, &rl0, &rl1));
     const bool evaluate = mode == RUN_EXCHANGE || mode == RUN_EVALUATE;
     // the leaf quartets go through the shell screen (count pass only for RUN_COUNT)
     const bool screen = evaluate || mode == RUN_COUNT;
@@ -544,7 +574,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
     if (D == 0) {
         KX_TRY(grow(c, &c->d_scan, &c->scan_cap, 16));
         int64_t* d_n = c->d_scan;
-        k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], d_n);
+        k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], d_n, rl0, rl1);
         c->launches++;
         int64_t nk = 0;
         KX_CUDA(c, cudaMemcpyAsync(&nk, d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
@@ -565,7 +595,8 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
             int64_t* off = c->d_scan + nfront;
             unsigned g = (unsigned)std::min<int64_t>((nfront + 255) / 256, (int64_t)c->n_sm * 64);
             k_expand_mask<<<g, 256, 0, c->stream>>>(c->d_front[cur], nfront, child, nchild, nsys, lnext, S, Pn,
-                                                    o->tau, c->d_mask, cnt, nullptr, o->symmetric);
+                                                    o->tau, c->d_mask, cnt, nullptr, o->symmetric,
+                                                    row_range(c, o, k + 1));
             c->launches++;
             int64_t total = 0;
             KX_TRY(exclusive_scan(c, cnt, off, nfront, &total));
@@ -817,7 +848,9 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
     const double* S = c->d_nrm_s;
     const double* Pn = c->d_nrm_p;
     if (D == 0) {
-        k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], w + W.t(0));
+        int rl0 = 0, rl1 = 0;
+        KX_TRY(row_leaves(c, o, &rl0, &rl1));
+        k_root_only<<<1, 1, 0, c->stream>>>(c->d_lseg, ny, S, Pn, o->tau, c->d_front[0], w + W.t(0), rl0, rl1);
         c->launches++;
         KX_TRY(chunk_dev(c, o, W, cap, c->d_front[0], ny, w + W.t(0), P, K));
         if (o->symmetric) KX_TRY(mirror_k(c, K));
@@ -835,7 +868,7 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
         const int32_t* nsys = c->d_node_sys + c->levels[k].off;
         const Seg* lnext = c->d_lseg + (size_t)(k + 1) * ny;
         k_expand_mask<<<g, 256, 0, c->stream>>>(front, cap.mcap, child, nchild, nsys, lnext, S, Pn, o->tau,
-                                                c->d_mask, cnt, dn, o->symmetric);
+                                                c->d_mask, cnt, dn, o->symmetric, row_range(c, o, k + 1));
         c->launches++;
         KX_TRY(exclusive_scan_dev(c, cnt, off, cap.mcap, dn, w + W.t(k + 1)));
         if (k + 1 < D) {

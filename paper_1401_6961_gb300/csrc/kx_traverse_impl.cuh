@@ -8,6 +8,16 @@
 
 namespace kx {
 
+// A shard of the K rows: only row blocks A whose tree positions meet
+// [r0, r1) are traversed; lo/hi give the tree-position range [lo, hi) of
+// every node of the level the children live on.  lo == nullptr: all rows.
+struct RowRange {
+    const int32_t* lo;
+    const int32_t* hi;
+    int r0, r1;
+    __device__ bool keeps(int node) const { return !lo || (lo[node] < r1 && hi[node] > r0); }
+};
+
 // Survivor mask of the up to 16 children of task t = (A,B,C,D) one level
 // down (Eq. 7): bit ((iA*2 + iB)*2 + iC)*2 + iD is set iff
 //     beta = (||Q_{A'B'}|| * ||P_{B'D'}||) * ||Q_{C'D'}|| > tau
@@ -16,16 +26,19 @@ namespace kx {
 // diag (a symmetric build and A == C) only the children with iA <= iC are
 // tested: every child of a node left of another lies left of all of the
 // other's children, so the K blocks (A',C') with A' <= C' are exactly these.
+// Children whose row block A' lies outside `rows` are dropped.
 __device__ __forceinline__ unsigned task_child_mask(const Task t, const int32_t* __restrict__ child,
                                                     const int32_t* __restrict__ nchild,
                                                     const double* __restrict__ S, const double* __restrict__ Pn,
-                                                    int64_t t0, int nn, double tau, bool diag) {
+                                                    int64_t t0, int nn, double tau, bool diag,
+                                                    const RowRange rows) {
     const int ca = child[t.a], na = nchild[t.a];
     const int cb = child[t.b], nb = nchild[t.b];
     const int cc = child[t.c], nc = nchild[t.c];
     const int cd = child[t.d], nd = nchild[t.d];
     unsigned m = 0;
-    for (int ia = 0; ia < na; ++ia)
+    for (int ia = 0; ia < na; ++ia) {
+        if (!rows.keeps(ca + ia)) continue;
         for (int ib = 0; ib < nb; ++ib) {
             const double sab = S[t0 + (int64_t)(ca + ia) * nn + (cb + ib)];
             for (int id = 0; id < nd; ++id) {
@@ -36,6 +49,7 @@ __device__ __forceinline__ unsigned task_child_mask(const Task t, const int32_t*
                 }
             }
         }
+    }
     return m;
 }
 

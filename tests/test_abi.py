@@ -48,10 +48,10 @@ def test_default_opts(lib):
 
 def test_struct_layouts_match_header(lib):
     import paper_1401_6961_gb300 as kx
-    assert ctypes.sizeof(kx.kx_opts) == 48
+    assert ctypes.sizeof(kx.kx_opts) == 64
     assert ctypes.sizeof(kx.kx_basis) == 40
-    # 4 counters + 32 levels + 4 ints + 8 doubles
-    assert ctypes.sizeof(kx.kx_stats) == 8 * 4 + 8 * 32 + 4 * 4 + 8 * 8
+    # 4 counters + 32 levels + 4 ints + 11 doubles
+    assert ctypes.sizeof(kx.kx_stats) == 8 * 4 + 8 * 32 + 4 * 4 + 8 * 11
 
 
 def test_create_rejects_bad_basis_without_gpu(lib):
@@ -98,6 +98,13 @@ int main(void) {
     if (kx_n_functions(NULL) != -1) return 3;
     printf("%s\n", kx_last_error(NULL));
     kx_destroy(NULL);
+    {
+        /* host-only shard plan: the tie at the middle leaf goes to the lower boundary */
+        const double w[5] = {1.0, 1.0, 4.0, 1.0, 1.0};
+        int32_t b[3];
+        if (kx_shard_bounds(w, 5, 2, b) != KX_OK || b[0] != 0 || b[1] != 2 || b[2] != 5) return 4;
+    }
+    printf("%d %d %d\n", (int)sizeof(kx_opts), (int)sizeof(kx_stats), (int)sizeof(kx_basis));
     return 0;
 }
 """
@@ -109,6 +116,7 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     no device work)."""
     import shutil
     import subprocess
+    import paper_1401_6961_gb300 as kx
     from paper_1401_6961_gb300 import _binding
     gcc = shutil.which("gcc")
     if gcc is None:
@@ -122,4 +130,9 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
                         f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
-    assert r.returncode == 0 and r.stdout.strip() == "null context"
+    assert r.returncode == 0, r.returncode
+    lines = r.stdout.strip().splitlines()
+    assert lines[0] == "null context"
+    # the C compiler's struct sizes are the binding's
+    assert [int(x) for x in lines[1].split()] == [ctypes.sizeof(kx.kx_opts), ctypes.sizeof(kx.kx_stats),
+                                                  ctypes.sizeof(kx.kx_basis)]

@@ -64,10 +64,8 @@ def test_benchmark_and_sweep_members_keep_the_oo_floor():
 
 
 def test_alkane_bonds_and_counts():
-    """Bond lengths, backbone angles and counts.  (The torsions are drawn
-    independently, so longer chains are not self-avoiding: only bonded
-    geometry is pinned here.)"""
-    for n in (6, 14):
+    """Bond lengths, backbone angles and counts."""
+    for n in (3, 6, 14, 40):
         s = wl.alkane(n, 6000 + n)
         xyz = s.xyz * ANG
         c = xyz[:n]
@@ -84,6 +82,30 @@ def test_alkane_bonds_and_counts():
             assert ang == pytest.approx(wl.TETRAHEDRAL, abs=1e-6)
         # small basis: C carries the O shells (9 functions), H 2 s shells
         assert s.n_fn == 9 * n + 2 * (2 * n + 2)
+
+
+def test_alkanes_are_self_avoiding():
+    """No clashes in the chains of the learned-culling evaluation: carbons
+    three or more bonds apart are at least 2.4 Angstrom apart, every other
+    pair of atoms that is not bonded at least 1.5 Angstrom (a brute-force
+    check over all pairs, independent of the generator's own test)."""
+    for n in (10, 14, 20, 40, 80):
+        s = wl.alkane(n, 6000 + n)
+        xyz = s.xyz * ANG
+        carbon = [i for i in range(n)] + [0] * 3 + [i for i in range(1, n - 1) for _ in range(2)] + [n - 1] * 3
+        is_c = np.array([q == "C" for q in s.symbols])
+        d = np.linalg.norm(xyz[:, None] - xyz[None], axis=-1)
+        for i in range(s.n_atom):
+            for j in range(i + 1, s.n_atom):
+                if is_c[i] and is_c[j]:
+                    sep = abs(carbon[i] - carbon[j])
+                    if sep == 1:
+                        continue
+                    assert d[i, j] >= (2.4 if sep >= 3 else 1.5) - 1e-12, (n, i, j, d[i, j])
+                elif is_c[i] != is_c[j] and carbon[i] == carbon[j]:
+                    continue
+                else:
+                    assert d[i, j] >= 1.5 - 1e-12, (n, i, j, d[i, j])
 
 
 def test_density_is_symmetric_and_decays():

@@ -275,45 +275,121 @@ def _place_nerf(a: np.ndarray, b: np.ndarray, c: np.ndarray, bond: float,
     return c + d2[0] * bc + d2[1] * m + d2[2] * n
 
 
+ALKANE_MIN_CC = 2.4      # Angstrom: carbons three or more bonds apart
+ALKANE_MIN_NONBONDED = 1.5   # Angstrom: every other pair of atoms not bonded
+ALKANE_TRIES = 40        # torsion draws per carbon before stepping back one carbon
+
+
+def _alkane_hydrogens(c: List[np.ndarray], i: int) -> List[np.ndarray]:
+    """Hydrogen positions of carbon i of the chain c (its neighbours placed)."""
+    n = len(c)
+    nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+    if len(nb) == 2:
+        u = (c[i] - c[nb[0]]) + (c[i] - c[nb[1]])
+        u /= np.linalg.norm(u)
+        w = np.cross(c[nb[0]] - c[i], c[nb[1]] - c[i])
+        w /= np.linalg.norm(w)
+        half = math.radians(TETRAHEDRAL) / 2.0
+        return [c[i] + CH_BOND * (math.cos(half) * u + sgn * math.sin(half) * w) for sgn in (1.0, -1.0)]
+    j = nb[0]
+    # a reference atom for the torsion: the next carbon along, or a fixed
+    # off-axis point for ethane-like ends
+    k = [q for q in (j - 1, j + 1) if 0 <= q < n and q != i]
+    ref = c[k[0]] if k else c[j] + np.array([0.0, 1.0, 0.0])
+    return [_place_nerf(ref, c[j], c[i], CH_BOND, TETRAHEDRAL, tor) for tor in (60.0, 180.0, 300.0)]
+
+
+def _clashes(new: List[Tuple[np.ndarray, str, int]], old: List[Tuple[np.ndarray, str, int]]) -> bool:
+    """True if an atom of `new` sits too close to an atom of `new` or `old`.
+
+    Atoms are (position, element, carbon index: the carbon itself or the one
+    a hydrogen is bonded to).  Bonded pairs (C-C of neighbouring carbons, C-H
+    of a hydrogen and its carbon) are exempt; carbons three or more bonds
+    apart must be ALKANE_MIN_CC apart, every other pair ALKANE_MIN_NONBONDED.
+    """
+    pool = old + new
+    for ia, (x, ex, cx) in enumerate(new):
+        for jb, (y, ey, cy) in enumerate(pool):
+            if jb >= len(old) and jb - len(old) <= ia:
+                continue   # each pair of new atoms once, never an atom with itself
+            if ex == "C" and ey == "C":
+                if abs(cx - cy) <= 1:
+                    continue
+                lim = ALKANE_MIN_CC if abs(cx - cy) >= 3 else ALKANE_MIN_NONBONDED
+            elif ex != ey and cx == cy:
+                continue   # C-H bond
+            else:
+                lim = ALKANE_MIN_NONBONDED
+            if float(np.linalg.norm(x - y)) < lim:
+                return True
+    return False
+
+
 def alkane(n_carbon: int, seed: int, basis: str = "small") -> System:
-    """Linear alkane C_nH_{2n+2} with seeded torsions.
+    """Linear alkane C_nH_{2n+2} with seeded torsions, free of clashes.
 
     C-C 1.54, C-H 1.09 Angstrom, tetrahedral angles; backbone torsions are
-    drawn from {60, 180, 300} degrees plus a uniform +-15 degree jitter.
-    Carbon uses the oxygen shell set of the chosen basis.
+    drawn from {60, 180, 300} degrees plus a uniform +-15 degree jitter.  The
+    chain is self-avoiding: a torsion is drawn again when the carbon it
+    places, or the hydrogens it completes, would come closer than 2.4
+    Angstrom to a carbon three or more bonds away or 1.5 Angstrom to any
+    other atom it is not bonded to, and after ALKANE_TRIES draws the previous
+    carbon is drawn again.  Atoms: the carbons in chain order, then the
+    hydrogens carbon by carbon.  Carbon uses the oxygen shell set of the
+    chosen basis.
     """
+    if n_carbon < 3:
+        raise ValueError("alkane needs at least three carbons")
     rng = np.random.default_rng(seed)
-    c = [np.array([0.0, 0.0, 0.0]), np.array([CC_BOND, 0.0, 0.0])]
-    if n_carbon >= 3:
-        ang = math.radians(TETRAHEDRAL)
-        c.append(c[1] + CC_BOND * np.array([-math.cos(ang), math.sin(ang), 0.0]))
-    for i in range(3, n_carbon):
+    ang = math.radians(TETRAHEDRAL)
+    c = [np.array([0.0, 0.0, 0.0]), np.array([CC_BOND, 0.0, 0.0]),
+         np.array([CC_BOND, 0.0, 0.0]) + CC_BOND * np.array([-math.cos(ang), math.sin(ang), 0.0])]
+    # atoms placed by each step: step 2 = the first three carbons and the
+    # hydrogens of carbons 0 and 1; step i >= 3 = carbon i and the hydrogens
+    # of carbon i-1 (and of carbon i itself when it ends the chain)
+    steps: List[List[Tuple[np.ndarray, str, int]]] = []
+    first = [(c[k], "C", k) for k in range(3)]
+    first += [(h, "H", k) for k in ((0, 1, 2) if n_carbon == 3 else (0, 1)) for h in _alkane_hydrogens(c, k)]
+    if _clashes(first, []):
+        raise RuntimeError("alkane: clash in the first three carbons")
+    steps.append(first)
+    tries = [0] * (n_carbon + 1)
+    i = 3
+    draws = 0
+    while i < n_carbon:
+        draws += 1
+        if draws > 200000:
+            raise RuntimeError(f"alkane: no self-avoiding chain of {n_carbon} carbons found (seed {seed})")
+        if tries[i] >= ALKANE_TRIES:
+            # step back: the previous carbon is drawn again
+            tries[i] = 0
+            if i == 3:
+                raise RuntimeError(f"alkane: no self-avoiding chain of {n_carbon} carbons found (seed {seed})")
+            steps.pop()
+            c.pop()
+            i -= 1
+            continue
+        tries[i] += 1
         tor = float(rng.choice([60.0, 180.0, 300.0]) + rng.uniform(-15.0, 15.0))
-        c.append(_place_nerf(c[i - 3], c[i - 2], c[i - 1], CC_BOND, TETRAHEDRAL, tor))
-    c = c[:n_carbon]
-    syms = ["C"] * n_carbon
-    xyz = list(c)
-    for i in range(n_carbon):
-        nb = [j for j in (i - 1, i + 1) if 0 <= j < n_carbon]
-        if len(nb) == 2:
-            u = (c[i] - c[nb[0]]) + (c[i] - c[nb[1]])
-            u /= np.linalg.norm(u)
-            w = np.cross(c[nb[0]] - c[i], c[nb[1]] - c[i])
-            w /= np.linalg.norm(w)
-            half = math.radians(TETRAHEDRAL) / 2.0
-            for sgn in (1.0, -1.0):
-                syms.append("H")
-                xyz.append(c[i] + CH_BOND * (math.cos(half) * u + sgn * math.sin(half) * w))
-        else:
-            j = nb[0]
-            # a reference atom for the torsion: the next carbon along, or a
-            # fixed off-axis point for ethane-like ends
-            k = [q for q in (j - 1, j + 1) if 0 <= q < n_carbon and q != i]
-            ref = c[k[0]] if k else c[j] + np.array([0.0, 1.0, 0.0])
-            for tor in (60.0, 180.0, 300.0):
-                syms.append("H")
-                xyz.append(_place_nerf(ref, c[j], c[i], CH_BOND, TETRAHEDRAL, tor))
-    return build_system(f"C{n_carbon}H{2 * n_carbon + 2}", syms, np.stack(xyz), basis)
+        ci = _place_nerf(c[i - 3], c[i - 2], c[i - 1], CC_BOND, TETRAHEDRAL, tor)
+        trial = c + [ci]
+        new = [(ci, "C", i)] + [(h, "H", i - 1) for h in _alkane_hydrogens(trial, i - 1)]
+        if i == n_carbon - 1:
+            new += [(h, "H", i) for h in _alkane_hydrogens(trial, i)]
+        old = [a for st in steps for a in st]
+        if _clashes(new, old):
+            continue
+        c.append(ci)
+        steps.append(new)
+        i += 1
+        if i < n_carbon:
+            tries[i] = 0
+    atoms = [a for st in steps for a in st]
+    carbons = sorted((a for a in atoms if a[1] == "C"), key=lambda a: a[2])
+    hydrogens = sorted((a for a in atoms if a[1] == "H"), key=lambda a: a[2])   # stable: placement order
+    syms = ["C"] * n_carbon + ["H"] * len(hydrogens)
+    xyz = np.stack([a[0] for a in carbons] + [a[0] for a in hydrogens])
+    return build_system(f"C{n_carbon}H{2 * n_carbon + 2}", syms, xyz, basis)
 
 
 # ----------------------------------------------------------------------------
