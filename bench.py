@@ -39,6 +39,9 @@ TAU = 1e-10
 SPLIT = 5e-4          # measured max|dK| vs FP64: 3.0e-9 on (H2O)64, 1.7e-9 on the batch
 BENCH_LEAF = 16       # leaf size of the benchmark builds (fastest of 10, 16, 20, 32 on (H2O)64)
 L2_FLUSH_BYTES = 256 << 20
+# headline precision: FP32 below the split, FP64 above ("mixed") or double-word FP32 above ("mixed_dw")
+PRECISION = {"mixed": lambda kx: kx.KX_MIXED, "mixed_dw": lambda kx: kx.KX_MIXED_DW}
+DTYPE = {"mixed": "f32+f64", "mixed_dw": "f32+dw32+f64"}
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
            0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
@@ -108,10 +111,13 @@ class ClockSampler:
 
 
 def kernel_name(kx, ctx, s: int) -> str:
-    """Name of the kernel that runs stream s (precision * 81 + class)."""
+    """Name of the kernel that runs stream s (precision * 81 + class;
+    precision 0 FP64, 1 FP32, 2 double-word FP32)."""
     cls = s % 81
     la, lb, lc, ld = cls // 27, (cls // 9) % 3, (cls // 3) % 3, cls % 3
     args = f"{la},{lb},{lc},{ld}"
+    if s >= 162:
+        return f"k_eri<{args},kx::dw>"
     if la + lb + lc + ld < 7:
         return f"k_eri<{args},{'double' if s < 81 else 'float'}>"
     variant = int(kx.kx_get_launch_shapes(ctx)[2][s])
@@ -247,7 +253,7 @@ def workload_config(sys_, precision, name, symmetric=True, leaf_max=10):
                         f"({sys_.n_fn} functions, {sys_.n_shell} shells), tau=1e-10",
             "name": name,
             "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": leaf_max,
-            "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
+            "precision": precision, "split_threshold": SPLIT if precision.startswith("mixed") else None,
             "shell_screen": True, "symmetric": bool(symmetric),
             "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB buffer written)",
             "parallelism": "replicas"}
@@ -260,7 +266,7 @@ def batch_config(systems, precision, symmetric=True, leaf_max=10):
                         f"{sum(s.n_fn for s in systems)} functions in all), each with its own density, "
                         f"tau={BATCH_TAU:g}",
             "name": "batch256", "systems": len(systems), "tau": BATCH_TAU, "leaf_max": leaf_max,
-            "precision": precision, "split_threshold": SPLIT if precision == "mixed" else None,
+            "precision": precision, "split_threshold": SPLIT if precision.startswith("mixed") else None,
             "shell_screen": True, "symmetric": bool(symmetric),
             "launch": "one captured CUDA graph per batch build (autotuned class-kernel shapes)",
             "l2": "inputs larger than L2 (packed P and K 297 MB each), and a 256 MB buffer written between steps",
@@ -293,7 +299,7 @@ def run_batch(args):
     Kd = torch.empty_like(Pd)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sym = 0 if args.no_symmetric else 1
-    mixed = dict(tau=BATCH_TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, symmetric=sym)
+    mixed = dict(tau=BATCH_TAU, precision=PRECISION[args.precision](kx), split_threshold=SPLIT, symmetric=sym)
 
 
     # set-up (untimed): launch-shape autotuning, then the captured plan
@@ -376,10 +382,11 @@ def run_batch(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": batch_config(systems, "mixed", sym, args.leaf_max),
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": batch_config(systems, args.precision, sym, args.leaf_max),
             "quartets_per_s": ws * st.n_shell_quartets / (ms_step * 1e-3),
             "shell_quartets": st.n_shell_quartets, "leaf_quartets": st.n_leaf_quartets,
-            "shell_quartets_fp64": st.n_shell_quartets_fp64,
+            "shell_quartets_fp64": st.n_shell_quartets_fp64, "shell_quartets_dw": st.n_shell_quartets_dw,
             "stages_ms_eager": {"norms": ste.ms_norms, "traverse": ste.ms_traverse, "expand": ste.ms_expand,
                                 "eri": ste.ms_eri, "total": ste.ms_total},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -426,7 +433,8 @@ def run_ours(args):
     Kd = torch.empty((n, n), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sym = 0 if args.no_symmetric else 1
-    mixed = dict(tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, profile=1, symmetric=sym)
+    prec = PRECISION[args.precision](kx)
+    mixed = dict(tau=TAU, precision=prec, split_threshold=SPLIT, profile=1, symmetric=sym)
     plain = dict(tau=TAU, precision=kx.KX_FP64, profile=1, symmetric=sym)
 
 
@@ -506,7 +514,7 @@ def run_ours(args):
     eri_ms = float(prof["ms"].sum())
     # every class stream of the eager builds, on stderr
     streams = []
-    for s_ in range(162):
+    for s_ in range(kx.NSTREAM):
         if prof["ms"][s_] > 0:
             c_ = s_ % 81
             streams.append({"stream": s_, "class": "({}{}|{}{})".format(*("spd"[x] for x in (
@@ -559,11 +567,11 @@ def run_ours(args):
     if args.e2e_steps > 0:
         Ph = torch.from_numpy(P).pin_memory().numpy()
         Kh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
-        ex.host(Ph, tau=TAU, precision=kx.KX_MIXED, split_threshold=SPLIT, symmetric=sym)
+        ex.host(Ph, tau=TAU, precision=prec, split_threshold=SPLIT, symmetric=sym)
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(tau=TAU, precision=kx.KX_MIXED,
+            kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(tau=TAU, precision=prec,
                                                                split_threshold=SPLIT, symmetric=sym), Kh)
         dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
         e2e = {"value": ws * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
@@ -578,11 +586,11 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": workload_config(sys_, "mixed", args.workload, sym, args.leaf_max),
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": workload_config(sys_, args.precision, args.workload, sym, args.leaf_max),
             "quartets_per_s": ws * quartets / (ms_step * 1e-3),
             "shell_quartets": quartets, "leaf_quartets": st.n_leaf_quartets,
-            "shell_quartets_fp64": st.n_shell_quartets_fp64,
+            "shell_quartets_fp64": st.n_shell_quartets_fp64, "shell_quartets_dw": st.n_shell_quartets_dw,
             "launch": "one captured CUDA graph per build (kx_graph_plan / kx_graph_launch), autotuned "
                       f"class-kernel shapes ({n_tuned} streams tuned)",
             "eager": {"value": ws * 1e3 / ms_e, "unit": UNIT, "ms_per_step": ms_e,
@@ -815,6 +823,8 @@ def main():
     ap.add_argument("--workload", choices=WORKLOADS, default="water64",
                     help="water64 is the benchmark; water16 is a small case for profiling; batch256 is the "
                          "batched workload (256 clusters per step, captured graph)")
+    ap.add_argument("--precision", choices=sorted(PRECISION), default="mixed",
+                    help="headline build: FP32 below the split and FP64 (mixed) or double-word FP32 (mixed_dw) above")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--eager-steps", type=int, default=1, help="profiled eager builds after the timed replays")
     ap.add_argument("--e2e-steps", type=int, default=2)

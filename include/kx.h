@@ -51,7 +51,16 @@ enum {
     KX_ENOTIMPL = 7    /* option not available in this build */
 };
 
-enum { KX_FP64 = 0, KX_MIXED = 1 };
+/* Precision of the ERI stage.  KX_FP64: every shell quartet in FP64.
+ * KX_MIXED: quartets with beta <= split_threshold in FP32 (FP32 Boys
+ * table, pair data, P copy and accumulation), the rest in FP64.
+ * KX_MIXED_DW: the same split, with the quartets above it in double-word
+ * FP32 arithmetic (each value an unevaluated sum of two floats, about 48
+ * significant bits, all on the FP32 pipe) wherever the class has such a
+ * kernel (la+lb+lc+ld <= 5) and in FP64 otherwise; split_threshold = 0
+ * puts every quartet of those classes in double-word arithmetic.  K is
+ * accumulated in FP64 in every mode. */
+enum { KX_FP64 = 0, KX_MIXED = 1, KX_MIXED_DW = 2 };
 
 typedef struct kx_ctx kx_ctx;          /* opaque, owned by the library */
 
@@ -68,8 +77,9 @@ typedef struct {
 /* Options of one exchange build. */
 typedef struct {
     double tau;                  /* Eq. 8 threshold tau_2e >= 0 (keep iff beta > tau) */
-    double split_threshold;      /* KX_MIXED: shell quartets with beta > split run in FP64 */
-    int32_t precision;           /* KX_FP64 or KX_MIXED */
+    double split_threshold;      /* KX_MIXED(_DW): shell quartets with beta > split run in FP64
+                                    (double-word FP32 in KX_MIXED_DW) */
+    int32_t precision;           /* KX_FP64, KX_MIXED or KX_MIXED_DW */
     int32_t shell_screen;        /* 1: apply Eq. 8 again to each shell quartet of a leaf */
     int32_t keep_worklist;       /* 1: retain the leaf-quartet list for kx_get_worklist */
     int32_t profile;             /* 1: time every ERI class launch (see kx_get_profile) */
@@ -81,7 +91,7 @@ typedef struct {
     int32_t row_leaf_hi;         /* the leaves [row_leaf_lo, row_leaf_hi) are traversed and
                                     evaluated (0, 0 = every leaf); see kx_row_work */
     int32_t reserved;            /* 0 */
-    double split_budget;         /* KX_MIXED, > 0: split_threshold is ignored and the split is
+    double split_budget;         /* KX_MIXED(_DW), > 0: split_threshold is ignored and the split is
                                     chosen per build from the FP32 error model so that the
                                     estimated max|dK| of the FP32 quartets stays within this
                                     budget (kx_stats.split_used, fp32_err_estimate) */
@@ -93,6 +103,7 @@ typedef struct {
     int64_t n_shell_quartets;    /* shell quartets evaluated */
     int64_t n_shell_quartets_fp64;
     int64_t n_candidates;        /* shell quartets screened at the shell level */
+    int64_t n_shell_quartets_dw; /* KX_MIXED_DW: shell quartets in double-word FP32 */
     int64_t n_tasks[32];         /* tasks surviving at each traversal level */
     int32_t depth;               /* deepest traversal level */
     int32_t n_chunks;
@@ -100,6 +111,7 @@ typedef struct {
     int32_t pad;
     double flops_fp64;           /* algorithmic FLOPs of the ERI+contraction stage */
     double flops_fp32;
+    double flops_dw;
     double ms_norms;             /* P norms and pyramid */
     double ms_traverse;          /* levels 0 .. depth-1 */
     double ms_expand;            /* last level + shell screen + class binning */
@@ -159,12 +171,31 @@ int kx_exchange_host(kx_ctx* c, const double* P_host, int64_t ldp, const kx_opts
  * 7-8) and the shell-level screen of kx_exchange for the same P and
  * options, but no integral is evaluated and K is not touched.  Fills
  * n_leaf_quartets, n_tasks, depth, n_candidates, n_shell_quartets,
- * n_shell_quartets_fp64 (KX_MIXED: those above split_threshold) and
- * flops_fp64/flops_fp32 (the ERI stage's algorithmic FLOPs), exactly as the
+ * n_shell_quartets_fp64 / _dw (KX_MIXED(_DW): those above split_threshold)
+ * and flops_fp64/flops_fp32/flops_dw (the ERI stage's algorithmic FLOPs), exactly as the
  * build would report them; the time fields hold the traversal and screen.
  * P: DEVICE, as for kx_exchange (ldp >= n_fn), or packed per system with
  * ldp = 0 on a batch context.  st is required.  Synchronous. */
 int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats* st);
+
+/* The split threshold of a mixed build from an error budget (a growth
+ * direction beyond the paper, whose integrals are all FP64).  An FP32 shell quartet
+ * q of bound beta_q (Eq. 8) perturbs its K shell block (a,c) by at most
+ * c_max eps32 beta_q and by c_rms eps32 beta_q in root-mean-square, with
+ * per-class constants measured on GB300 (eps32 = 2^-24).  A statistics
+ * variant of the build's count pass sums, for a sample of K shell blocks
+ * (every diagonal block, every pair of tree neighbours, 4 n_shell seeded
+ * random blocks), the FP32 quartets' c_max beta and (c_rms beta)^2 in bins
+ * of log2 beta.  The split is the largest tau * 2^k whose estimate
+ * 5 eps32 max_ac sqrt(sum (c_rms beta)^2) over those blocks is at most
+ * `budget`: st->split_used, st->fp32_err_estimate (that estimate) and
+ * st->fp32_err_bound (eps32 max_ac sum c_max beta, the bound under the
+ * per-quartet model).  0 when even the smallest split exceeds the budget.
+ * P and o as for kx_count (o->split_threshold and precision are ignored).
+ * Single-system contexts (KX_ENOTIMPL on a batch).  Synchronous.
+ * kx_exchange, kx_count and kx_graph_plan run this first when
+ * o->split_budget > 0 and build with the split it chooses. */
+int kx_split_plan(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double budget, kx_stats* st);
 
 /* K row-block shards (several GPUs).  The leaf quartets are independent,
  * so the build splits by the row block A of K (mu in A): a build with
@@ -231,13 +262,13 @@ int64_t kx_packed_size(const kx_ctx* c);
  * context.  *n_tuned = streams tuned (may be NULL). */
 int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int32_t* n_tuned);
 
-/* Current launch shape of the 162 streams (threads per block; persistent
+/* Current launch shape of the 243 streams (threads per block; persistent
  * blocks per SM, 0 = one thread per quartet; kernel variant: 0 for every
  * stream except the classes with la+lb+lc+ld >= 7, where FP64 has 0 the
  * rolled kernel, 1 the shared-memory kernel and 2 the shared-memory kernel
  * with the ket Hermite set pruned per ket component, and FP32 has 0 the
- * shared-memory kernel and 1 its ket-pruned form).  Host arrays, may be
- * NULL. */
+ * shared-memory kernel and 1 its ket-pruned form; the double-word streams
+ * have one kernel each).  Host arrays of 243 entries, may be NULL. */
 int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm, int32_t* variant);
 
 /* Sets the launch shape of stream s = precision * 81 + class: threads a
@@ -293,10 +324,11 @@ int kx_get_worklist(kx_ctx* c, const int32_t* a_filter, int32_t n_filter,
 int kx_get_norms(kx_ctx* c, double* s2, double* pq);
 
 /* Per-stream totals of the last kx_exchange run with profile = 1, for the
- * 162 streams s = precision * 81 + class (precision 0 = FP64, 1 = FP32;
- * class = ((la*3 + lb)*3 + lc)*3 + ld): ms = summed CUDA-event time of the
- * stream's kernel launches, n = shell quartets, flops = algorithmic FLOPs,
- * launches = kernel launches.  Host arrays of 162 entries (any may be NULL). */
+ * 243 streams s = precision * 81 + class (precision 0 = FP64, 1 = FP32,
+ * 2 = double-word FP32; class = ((la*3 + lb)*3 + lc)*3 + ld): ms = summed
+ * CUDA-event time of the stream's kernel launches, n = shell quartets,
+ * flops = algorithmic FLOPs, launches = kernel launches.  Host arrays of
+ * 243 entries (any may be NULL). */
 int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32_t* launches);
 
 /* Throughput probe on `device`, timed with CUDA events (best of five after

@@ -15,7 +15,8 @@ import numpy as np
 from .build import LIB
 
 KX_OK, KX_EINVAL, KX_ESTATE, KX_ENOMEM, KX_ECUDA, KX_ECAPACITY, KX_ETIMEOUT, KX_ENOTIMPL = range(8)
-KX_FP64, KX_MIXED = 0, 1
+KX_FP64, KX_MIXED, KX_MIXED_DW = 0, 1, 2
+NSTREAM = 243   # class-kernel streams: precision (FP64, FP32, double word) * 81 + class
 ERROR_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ESTATE", 3: "KX_ENOMEM", 4: "KX_ECUDA",
                5: "KX_ECAPACITY", 6: "KX_ETIMEOUT", 7: "KX_ENOTIMPL"}
 
@@ -27,7 +28,7 @@ EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", 
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
            "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
            "kx_block_norms", "kx_mlp_infer_bf16", "kx_mlp_loss_grad", "kx_mlp_adam",
-           "kx_row_work", "kx_shard_bounds", "kx_last_error", "kx_destroy"]
+           "kx_row_work", "kx_shard_bounds", "kx_split_plan", "kx_last_error", "kx_destroy"]
 KX_NFEAT = 10
 KX_MLP_HIDDEN = 64
 KX_MLP_NPARAM = 9109
@@ -56,9 +57,10 @@ class kx_opts(ctypes.Structure):
 class kx_stats(ctypes.Structure):
     _fields_ = [("n_leaf_quartets", ctypes.c_int64), ("n_shell_quartets", ctypes.c_int64),
                 ("n_shell_quartets_fp64", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("n_shell_quartets_dw", ctypes.c_int64),
                 ("n_tasks", ctypes.c_int64 * 32), ("depth", ctypes.c_int32), ("n_chunks", ctypes.c_int32),
                 ("n_launches", ctypes.c_int32), ("pad", ctypes.c_int32), ("flops_fp64", ctypes.c_double),
-                ("flops_fp32", ctypes.c_double), ("ms_norms", ctypes.c_double),
+                ("flops_fp32", ctypes.c_double), ("flops_dw", ctypes.c_double), ("ms_norms", ctypes.c_double),
                 ("ms_traverse", ctypes.c_double), ("ms_expand", ctypes.c_double),
                 ("ms_eri", ctypes.c_double), ("ms_eri_kernel_max", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("split_used", ctypes.c_double),
@@ -122,6 +124,8 @@ def load() -> ctypes.CDLL:
     L.kx_get_profile.argtypes = [vp, _f64p, _i64p, _f64p, _i32p]
     L.kx_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _f64p]
     L.kx_row_work.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), _f64p]
+    L.kx_split_plan.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), ctypes.c_double,
+                                ctypes.POINTER(kx_stats)]
     L.kx_shard_bounds.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int32, _i32p]
     L.kx_traverse_level_noalloc.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_double, vp,
                                             ctypes.c_int64, _i64p]
@@ -229,10 +233,10 @@ def kx_autotune(ctx, P_ptr: int, opts: kx_opts, K_ptr: int) -> Tuple[kx_stats, i
 
 
 def kx_get_launch_shapes(ctx) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """(threads, blocks per SM, kernel variant) of the 162 streams."""
-    t = np.zeros(162, dtype=np.int32)
-    b = np.zeros(162, dtype=np.int32)
-    v = np.zeros(162, dtype=np.int32)
+    """(threads, blocks per SM, kernel variant) of the NSTREAM streams."""
+    t = np.zeros(NSTREAM, dtype=np.int32)
+    b = np.zeros(NSTREAM, dtype=np.int32)
+    v = np.zeros(NSTREAM, dtype=np.int32)
     _check(ctx, load().kx_get_launch_shapes(ctx, _p(t, _i32p), _p(b, _i32p), _p(v, _i32p)))
     return t, b, v
 
@@ -337,12 +341,12 @@ def kx_get_norms(ctx, n_shell: int, with_p: bool = True, total: Optional[int] = 
 
 
 def kx_get_profile(ctx) -> dict:
-    """Per-stream totals of the last profiled build: arrays of 162 entries
+    """Per-stream totals of the last profiled build: arrays of NSTREAM entries
     indexed by precision * 81 + class (precision 0 = FP64)."""
-    ms = np.zeros(162)
-    n = np.zeros(162, dtype=np.int64)
-    fl = np.zeros(162)
-    la = np.zeros(162, dtype=np.int32)
+    ms = np.zeros(NSTREAM)
+    n = np.zeros(NSTREAM, dtype=np.int64)
+    fl = np.zeros(NSTREAM)
+    la = np.zeros(NSTREAM, dtype=np.int32)
     _check(ctx, load().kx_get_profile(ctx, _p(ms, _f64p), _p(n, _i64p), _p(fl, _f64p), _p(la, _i32p)))
     return {"ms": ms, "n": n, "flops": fl, "launches": la}
 
@@ -364,6 +368,15 @@ def kx_row_work(ctx, P_ptr: int, ldp: int, opts: kx_opts) -> np.ndarray:
     w = np.zeros(n_leaf)
     _check(ctx, load().kx_row_work(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts), _p(w, _f64p)))
     return w
+
+
+def kx_split_plan(ctx, P_ptr: int, ldp: int, opts: kx_opts, budget: float) -> kx_stats:
+    """Split threshold from the FP32 error model (split_used,
+    fp32_err_estimate, fp32_err_bound of the returned stats)."""
+    st = kx_stats()
+    _check(ctx, load().kx_split_plan(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts), float(budget),
+                                     ctypes.byref(st)))
+    return st
 
 
 def _n_leaves(ctx):
@@ -543,6 +556,12 @@ class Exchange:
         import torch
         assert P.is_cuda and P.dtype == torch.float64 and P.stride(1) == 1 and P.shape == (self.n_fn, self.n_fn)
         return kx_row_work(self.ctx, P.data_ptr(), P.stride(0), kx_default_opts(**opts))
+
+    def split_plan(self, P, budget: float, **opts) -> kx_stats:
+        """The split of a mixed build of P whose FP32 error estimate fits `budget`."""
+        import torch
+        assert P.is_cuda and P.dtype == torch.float64 and P.stride(1) == 1 and P.shape == (self.n_fn, self.n_fn)
+        return kx_split_plan(self.ctx, P.data_ptr(), P.stride(0), kx_default_opts(**opts), budget)
 
     def worklist(self, a_filter=None) -> np.ndarray:
         return kx_get_worklist(self.ctx, a_filter)

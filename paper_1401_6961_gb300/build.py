@@ -54,6 +54,18 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def _weight(src: str) -> int:
+    """Rough compile cost of a translation unit: the per-bra-class ERI units
+    grow with the bra's angular momentum (the double-word ones stop at
+    la+lb+lc+ld = 5, so their heaviest bras are the middle ones)."""
+    b = os.path.basename(src)
+    for pre, base in (("kx_eri_dw_", 2), ("kx_eri_", 4)):
+        if b.startswith(pre) and b[len(pre):len(pre) + 2].isdigit():
+            la, lb = int(b[len(pre)]), int(b[len(pre) + 1])
+            return base + (la + lb if pre == "kx_eri_" else min(la + lb, 5 - la - lb) + 1)
+    return 6 if b.startswith("kx_eri_big") else 0
+
+
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     """Compile (if needed) and link libkx.so; returns its path."""
     os.makedirs(OBJ, exist_ok=True)
@@ -66,9 +78,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             todo.append(s)
     if todo:
         # heaviest translation units first
-        todo.sort(key=lambda s: ("kx_eri_" not in s, s), reverse=False)
-        todo.sort(key=lambda s: -sum(int(ch) for ch in os.path.basename(s)[7:9])
-                  if os.path.basename(s).startswith("kx_eri_") and os.path.basename(s)[7:9].isdigit() else 0)
+        todo.sort(key=lambda s: -_weight(s))
         n = jobs or max(1, min(len(todo), os.cpu_count() or 4))
         with cf.ThreadPoolExecutor(n) as ex:
             list(ex.map(lambda s: _compile(s, verbose), todo))

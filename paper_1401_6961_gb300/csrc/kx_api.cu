@@ -66,13 +66,14 @@ void free_all(kx_ctx* c) {
                     c->d_mask, c->d_scan, c->d_rec, c->d_bin, c->d_counters, c->d_keep, c->d_P32, c->d_scantmp,
                     c->d_hostP, c->d_hostK, c->d_leafdesc, c->d_list, c->d_sseg, c->d_tsys, c->d_lseg,
                     c->d_node_sys, c->d_mframe, c->d_gw, c->d_groots, c->d_gactive, c->d_tuneK,
-                    c->d_fseg, c->d_ftpos};
+                    c->d_fseg, c->d_ftpos, c->d_boysdw, c->d_Pdw, c->d_work, c->d_sflops};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < NPAIRCLASS; ++i) {
         if (c->d_pairmeta[i]) cudaFree(c->d_pairmeta[i]);
         if (c->d_pair64[i]) cudaFree(c->d_pair64[i]);
         if (c->d_pair32[i]) cudaFree(c->d_pair32[i]);
+        if (c->d_pairdw[i]) cudaFree(c->d_pairdw[i]);
     }
 }
 
@@ -158,7 +159,7 @@ int kx_create_batch(kx_ctx** out, int32_t n_sys, const kx_basis* bases, int devi
         c->sp_total += (int64_t)b->n_shell * b->n_shell;
     }
     c->n_fn = c->fn_off.back();
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    for (int s = 0; s < NSTREAM; ++s) {
         c->eri_threads[s] = ERI_THREADS;
         c->eri_bpsm[s] = 0;
         c->eri_variant[s] = 0;
@@ -257,24 +258,38 @@ int exchange_impl(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, dou
                   kx_stats* st) {
     if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
     if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
-    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
-    if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
+    if (o->precision < KX_FP64 || o->precision > KX_MIXED_DW) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision != KX_FP64 && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
         return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
     if (o->chunk_records < 0) return set_err(c, KX_EINVAL, "chunk_records must be >= 0");
     if (o->symmetric != 0 && o->symmetric != 1) return set_err(c, KX_EINVAL, "symmetric must be 0 or 1");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    if (!std::isfinite(o->split_budget) || o->split_budget < 0.0)
+        return set_err(c, KX_EINVAL, "split_budget must be >= 0");
     kx_stats local;
     kx_stats* s = st ? st : &local;
     std::memset(s, 0, sizeof(*s));
+    // a split from the error budget: plan first, then build with it
+    kx_opts ob = *o;
+    kx_stats sp;
+    std::memset(&sp, 0, sizeof(sp));
+    if (o->precision != KX_FP64 && o->split_budget > 0.0) {
+        KX_TRY(split_plan(c, P, ldp, o, o->split_budget, &sp));
+        ob.split_threshold = sp.split_used;
+        ob.split_budget = 0.0;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, c->stream);
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
-    int r = traverse_and_evaluate(c, P, ldp, o, K, ldk, s);
+    int r = traverse_and_evaluate(c, P, ldp, &ob, K, ldk, s);
+    s->split_used = o->precision != KX_FP64 ? ob.split_threshold : 0.0;
+    s->fp32_err_estimate = sp.fp32_err_estimate;
+    s->fp32_err_bound = sp.fp32_err_bound;
     cudaEventRecord(e1, c->stream);
     if (r == KX_OK) {
         cudaError_t e = cudaEventSynchronize(e1);
@@ -334,17 +349,31 @@ int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats
     if (c->n_sys == 1 ? ldp < c->n_fn : ldp != 0)
         return set_err(c, KX_EINVAL, "ldp must be >= n_fn (0 for the packed P of a batch)");
     if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
-    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
-    if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
+    if (o->precision < KX_FP64 || o->precision > KX_MIXED_DW) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision != KX_FP64 && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
         return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
     if (o->symmetric != 0 && o->symmetric != 1) return set_err(c, KX_EINVAL, "symmetric must be 0 or 1");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    if (!std::isfinite(o->split_budget) || o->split_budget < 0.0)
+        return set_err(c, KX_EINVAL, "split_budget must be >= 0");
     std::memset(st, 0, sizeof(*st));
+    kx_opts ob = *o;
+    kx_stats sp;
+    std::memset(&sp, 0, sizeof(sp));
+    if (o->precision != KX_FP64 && o->split_budget > 0.0) {
+        KX_TRY(split_plan(c, P, ldp, o, o->split_budget, &sp));
+        ob.split_threshold = sp.split_used;
+        ob.split_budget = 0.0;
+    }
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
-    return drive(c, RUN_COUNT, P, ldp, o, nullptr, 0, st, nullptr, 0);
+    const int r = drive(c, RUN_COUNT, P, ldp, &ob, nullptr, 0, st, nullptr, 0);
+    st->split_used = o->precision != KX_FP64 ? ob.split_threshold : 0.0;
+    st->fp32_err_estimate = sp.fp32_err_estimate;
+    st->fp32_err_bound = sp.fp32_err_bound;
+    return r;
 }
 
 int kx_row_work(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double* work) {
@@ -355,8 +384,8 @@ int kx_row_work(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, doubl
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
     if (!c->d_sflops) {
-        float h[2 * NCLASS];
-        for (int s = 0; s < 2 * NCLASS; ++s) h[s] = (float)class_flops(s % NCLASS);
+        float h[NSTREAM];
+        for (int s = 0; s < NSTREAM; ++s) h[s] = (float)class_flops(s % NCLASS);
         KX_CUDA(c, cudaMalloc(&c->d_sflops, sizeof(h)));
         KX_CUDA(c, cudaMemcpy(c->d_sflops, h, sizeof(h), cudaMemcpyHostToDevice));
     }
@@ -397,6 +426,21 @@ int kx_shard_bounds(const double* work, int32_t n_leaf, int32_t n_shards, int32_
     return KX_OK;
 }
 
+int kx_split_plan(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double budget, kx_stats* st) {
+    KX_TRY(check_ctx(c));
+    if (!P || !o || !st) return set_err(c, KX_EINVAL, "null argument");
+    if (c->n_sys == 1 ? ldp < c->n_fn : true) return set_err(c, KX_EINVAL, "ldp must be >= n_fn");
+    if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
+    if (o->symmetric != 0 && o->symmetric != 1) return set_err(c, KX_EINVAL, "symmetric must be 0 or 1");
+    if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    std::memset(st, 0, sizeof(*st));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
+    KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
+    return split_plan(c, P, ldp, o, budget, st);
+}
+
 int kx_exchange_batch(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st) {
     KX_TRY(check_ctx(c));
     return exchange_impl(c, P, 0, o, K, 0, st);
@@ -428,7 +472,7 @@ int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stat
     KX_TRY(check_ctx(c));
     if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
     if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
-    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision < KX_FP64 || o->precision > KX_MIXED_DW) return set_err(c, KX_EINVAL, "bad precision");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
@@ -445,7 +489,7 @@ int kx_autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stat
 
 int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_sm, int32_t* variant) {
     if (!c) return KX_EINVAL;
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    for (int s = 0; s < NSTREAM; ++s) {
         if (threads) threads[s] = c->eri_threads[s];
         if (blocks_per_sm) blocks_per_sm[s] = c->eri_bpsm[s];
         if (variant) variant[s] = c->eri_variant[s];
@@ -455,7 +499,7 @@ int kx_get_launch_shapes(const kx_ctx* c, int32_t* threads, int32_t* blocks_per_
 
 int kx_set_launch_shape(kx_ctx* c, int32_t s, int32_t threads, int32_t blocks_per_sm, int32_t variant) {
     KX_TRY(check_ctx(c));
-    if (s < 0 || s >= 2 * NCLASS || threads < 32 || threads > ERI_MAX_THREADS || threads % 32 || blocks_per_sm < 0)
+    if (s < 0 || s >= NSTREAM || threads < 32 || threads > ERI_MAX_THREADS || threads % 32 || blocks_per_sm < 0)
         return set_err(c, KX_EINVAL, "bad launch shape");
     if (variant < 0 || variant >= eri_kernel(s % NCLASS, s / NCLASS, 0).n_variants)
         return set_err(c, KX_EINVAL, "no such kernel variant for this stream");
@@ -470,20 +514,38 @@ int kx_graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, doubl
     KX_TRY(check_ctx(c));
     if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
     if (!std::isfinite(o->tau) || o->tau < 0.0) return set_err(c, KX_EINVAL, "tau must be >= 0");
-    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
-    if (o->precision == KX_MIXED && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
+    if (o->precision < KX_FP64 || o->precision > KX_MIXED_DW) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision != KX_FP64 && (!std::isfinite(o->split_threshold) || o->split_threshold < 0.0))
         return set_err(c, KX_EINVAL, "split_threshold must be >= 0");
     if (!std::isfinite(headroom) || headroom < 0.0 || headroom > 16.0)
         return set_err(c, KX_EINVAL, "headroom must be in [0, 16]");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
     DeviceGuard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
+    if (!std::isfinite(o->split_budget) || o->split_budget < 0.0)
+        return set_err(c, KX_EINVAL, "split_budget must be >= 0");
     kx_stats local;
     kx_stats* s = st ? st : &local;
     std::memset(s, 0, sizeof(*s));
+    // a split from the error budget is chosen once, for every replay
+    kx_opts ob = *o;
+    kx_stats sp;
+    std::memset(&sp, 0, sizeof(sp));
+    if (o->precision != KX_FP64 && o->split_budget > 0.0) {
+        KX_TRY(split_plan(c, P, 0, o, o->split_budget, &sp));
+        ob.split_threshold = sp.split_used;
+        ob.split_budget = 0.0;
+    }
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_CAND, 0, sizeof(unsigned long long), c->stream));
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
-    return graph_plan(c, P, o, K, headroom, s);
+    const int r = graph_plan(c, P, &ob, K, headroom, s);
+    c->graph_split = o->precision != KX_FP64 ? ob.split_threshold : 0.0;
+    c->graph_err_est = sp.fp32_err_estimate;
+    c->graph_err_bound = sp.fp32_err_bound;
+    s->split_used = c->graph_split;
+    s->fp32_err_estimate = c->graph_err_est;
+    s->fp32_err_bound = c->graph_err_bound;
+    return r;
 }
 
 int kx_graph_launch(kx_ctx* c, kx_stats* st) {
@@ -601,7 +663,7 @@ int kx_get_norms(kx_ctx* c, double* s2, double* pq) {
 
 int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32_t* launches) {
     if (!c) return KX_EINVAL;
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    for (int s = 0; s < NSTREAM; ++s) {
         if (ms) ms[s] = c->prof_ms[s];
         if (n) n[s] = c->prof_n[s];
         if (flops) flops[s] = c->prof_flops[s];

@@ -27,6 +27,7 @@
 
 #include <utility>
 
+#include "kx_dw.cuh"
 #include "kx_internal.cuh"
 
 namespace kx {
@@ -75,6 +76,26 @@ struct Real<float> {
     __device__ static float exp_(float x) { return expf(x); }
     __device__ static int rnd(float x) { return __float2int_rn(x); }
 };
+// Double-word FP32.  exp only enters the large-T Boys recursion as e^{-T}
+// with T >= 40, where it is below 3e-10 of the term it corrects, so its
+// FP32 value (relative error ~1e-7) is accurate far beyond double-word
+// precision there.
+template <>
+struct Real<dw> {
+    __device__ static dw sqrt_(dw x) { return dw_sqrt(x); }
+    __device__ static dw exp_(dw x) { return dw(expf(x.hi), 0.f); }
+    __device__ static int rnd(dw x) { return __float2int_rn(x.hi); }
+};
+
+// read-only loads of a value of the kernel's precision
+__device__ __forceinline__ double ld_(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_(const float* p) { return __ldg(p); }
+__device__ __forceinline__ dw ld_(const dw* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return dw(v.x, v.y);
+}
+__device__ __forceinline__ double shfl_up(unsigned mask, double v, int d) { return __shfl_up_sync(mask, v, d); }
+__device__ __forceinline__ float shfl_up(unsigned mask, float v, int d) { return __shfl_up_sync(mask, v, d); }
 
 // FP32 -> FP64 by bit manipulation (integer pipe), subnormals flushed.
 __device__ __forceinline__ double f2d_bits(float f) {
@@ -88,6 +109,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_f64(dw x) { return dw_to_f64(x); }
 
 // ---------------------------------------------------------------------------
 // Boys function and Hermite integrals
@@ -125,7 +147,7 @@ __device__ __forceinline__ void boys_scaled(R* G, R T, R rho, R r2, R pref, cons
             });
         } else {
             const R* row = tab + ig * (BOYS_M + 1);
-            sfor<L + 7>([&](auto k_) { rv[KX_CV(k_)] = __ldg(row + KX_CV(k_)); });
+            sfor<L + 7>([&](auto k_) { rv[KX_CV(k_)] = ld_(row + KX_CV(k_)); });
         }
         R s = pref;
         const R m2r = R(-2) * rho;
@@ -252,15 +274,15 @@ __device__ __forceinline__ void load_pairs(const R* __restrict__ pb, const R* __
                                            R& qq, R& kab, R& kcd, R& X, R& Y, R& Z) {
     constexpr int EAB = etab(LA, LB), ECD = etab(LC, LD);
     if constexpr (sizeof(R) == 8) {
-        sfor<3 * EAB>([&](auto k_) { eab[KX_CV(k_)] = __ldg(pb + 5 + KX_CV(k_)); });
-        sfor<3 * ECD>([&](auto k_) { ecd[KX_CV(k_)] = __ldg(pk + 5 + KX_CV(k_)); });
-        p = __ldg(pb);
-        qq = __ldg(pk);
-        X = __ldg(pb + 1) - __ldg(pk + 1);
-        Y = __ldg(pb + 2) - __ldg(pk + 2);
-        Z = __ldg(pb + 3) - __ldg(pk + 3);
-        kab = __ldg(pb + 4);
-        kcd = __ldg(pk + 4);
+        sfor<3 * EAB>([&](auto k_) { eab[KX_CV(k_)] = ld_(pb + 5 + KX_CV(k_)); });
+        sfor<3 * ECD>([&](auto k_) { ecd[KX_CV(k_)] = ld_(pk + 5 + KX_CV(k_)); });
+        p = ld_(pb);
+        qq = ld_(pk);
+        X = ld_(pb + 1) - ld_(pk + 1);
+        Y = ld_(pb + 2) - ld_(pk + 2);
+        Z = ld_(pb + 3) - ld_(pk + 3);
+        kab = ld_(pb + 4);
+        kcd = ld_(pk + 4);
     } else {
         const float4* b4 = reinterpret_cast<const float4*>(pb);
         const float4* k4 = reinterpret_cast<const float4*>(pk);
@@ -361,7 +383,7 @@ __device__ __forceinline__ void contract_a(R* kacc, const R* Rt, const R* eab, c
             sfor<ND>([&](auto isig_) {
                 constexpr int isig = KX_CV(isig_);
                 constexpr int sx = cart_x(LD, isig), sy = cart_y(LD, isig), sz = cart_z(LD, isig);
-                const R pv = __ldg(prow + isig);
+                const R pv = ld_(prow + isig);
                 sfor<nx + sx + 1>([&](auto t_) {
                     constexpr int t = KX_CV(t_);
                     sfor<ny + sy + 1>([&](auto u_) {
@@ -456,7 +478,7 @@ __device__ __forceinline__ void contract_b(R* kacc, const R* Rt, const R* eab, c
             sfor<NB>([&](auto ilam_) {
                 constexpr int ilam = KX_CV(ilam_);
                 constexpr int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
-                const R pv = __ldg(Pb + ilam * ldp + isig);
+                const R pv = ld_(Pb + ilam * ldp + isig);
                 sfor<mx + lx + 1>([&](auto t_) {
                     constexpr int t = KX_CV(t_);
                     sfor<my + ly + 1>([&](auto u_) {
@@ -544,7 +566,7 @@ __device__ __forceinline__ void flush_k(R* kacc, int fa, int fc, double* __restr
         R v = kacc[e];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            R o = __shfl_up_sync(full, v, d);
+            R o = shfl_up(full, v, d);
             if (lane - d >= start) v += o;
         }
         if (tail && key >= 0) atomicAdd(Kb + (e / NC) * ldk + e % NC, to_f64(v));
@@ -665,7 +687,7 @@ __device__ __forceinline__ void contract_a_rolled(R* kacc, const R* Rt, const R*
 #pragma unroll 1
             for (int isig = 0; isig < ND; ++isig) {
                 const int sx = cart_x(LD, isig), sy = cart_y(LD, isig), sz = cart_z(LD, isig);
-                const R pv = __ldg(prow + isig);
+                const R pv = ld_(prow + isig);
 #pragma unroll 1
                 for (int t = 0; t <= nx + sx; ++t)
 #pragma unroll 1
@@ -736,7 +758,7 @@ __device__ __forceinline__ void contract_b_rolled(R* kacc, const R* Rt, const R*
 #pragma unroll 1
             for (int ilam = 0; ilam < NB; ++ilam) {
                 const int lx = cart_x(LB, ilam), ly = cart_y(LB, ilam), lz = cart_z(LB, ilam);
-                const R pv = __ldg(Pb + ilam * ldp + isig);
+                const R pv = ld_(Pb + ilam * ldp + isig);
 #pragma unroll 1
                 for (int t = 0; t <= mx + lx; ++t)
 #pragma unroll 1
@@ -1354,6 +1376,29 @@ EriKern eri_kernel(int prec, int variant) {
                                     eri_flops<LA_, LB_, 2, 0>(), eri_flops<LA_, LB_, 2, 1>(),             \
                                     eri_flops<LA_, LB_, 2, 2>()};                                         \
         return f[cls % 9];                                                                               \
+    }
+
+// Double-word FP32 kernels (kx_dw.cuh) of the classes with la+lb+lc+ld <=
+// DW_LMAX; the larger classes have none (fully unrolled in double-word
+// arithmetic they take minutes each to compile and spill heavily) and run
+// their FP64 kernels instead.
+template <int LA, int LB, int LC, int LD>
+EriKern eri_kernel_dw() {
+    static_assert(DW_LMAX < ROLL_L, "double-word kernels are the unrolled ones");
+    if constexpr (LA + LB + LC + LD <= DW_LMAX) return {&k_eri<LA, LB, LC, LD, dw>, 0, 1};
+    else return {nullptr, 0, 0};
+}
+
+#define KX_ERI_DW_CASE(LA_, LB_, LC_, LD_) \
+    case LC_ * 3 + LD_: return eri_kernel_dw<LA_, LB_, LC_, LD_>();
+#define KX_ERI_DISPATCH_DW(LA_, LB_)                                                                     \
+    EriKern eri_kernel_dw_ab##LA_##LB_(int cls) {                                                        \
+        switch (cls % 9) {                                                                               \
+            KX_ERI_DW_CASE(LA_, LB_, 0, 0) KX_ERI_DW_CASE(LA_, LB_, 0, 1) KX_ERI_DW_CASE(LA_, LB_, 0, 2) \
+            KX_ERI_DW_CASE(LA_, LB_, 1, 0) KX_ERI_DW_CASE(LA_, LB_, 1, 1) KX_ERI_DW_CASE(LA_, LB_, 1, 2) \
+            KX_ERI_DW_CASE(LA_, LB_, 2, 0) KX_ERI_DW_CASE(LA_, LB_, 2, 1) KX_ERI_DW_CASE(LA_, LB_, 2, 2) \
+            default: return EriKern{nullptr, 0, 0};                                                      \
+        }                                                                                                \
     }
 
 }  // namespace kx

@@ -13,7 +13,7 @@
 // routes a kept quartet to the FP64 or the FP32 kernels in mixed mode.
 //
 // Records are binned by angular-momentum class and precision ("stream",
-// 162 of them).  One warp handles one leaf quartet; lanes walk its shell
+// 243 of them: FP64, FP32 and double word).  One warp handles one leaf quartet; lanes walk its shell
 // quartets with d fastest, then b, c, a, so runs of equal (a,c) -- one K
 // block -- stay adjacent in each stream.  A first pass counts the records of
 // every (stream, block); after a scan of those counts a second pass writes
@@ -44,14 +44,39 @@ struct ExpandArgs {
     const int32_t* pairmap;
     double tau, split;
     float ltau, lsplit;
-    int mixed, screen;
+    int mixed;               // the build's precision (KX_FP64, KX_MIXED, KX_MIXED_DW)
+    int screen;
     int sym;                 // symmetric build: inside a diagonal block (A == C) only a <= c
     // count pass only, may be null: work[A] += the algorithmic FLOPs of the
     // kept shell quartets of every leaf quartet with row leaf A (sflops[s]
     // = FLOPs of one quartet of stream s)
     double* work;
     const float* sflops;
+    // statistics pass (split planning): for every FP32 quartet of a sampled
+    // K shell block (blkslot[(a,c)] >= 0), in bin j = floor(log2 beta -
+    // lbin0) clamped to [0, nbin): acc[(slot * nbin + j) * 2] += cmax[cls]
+    // beta and acc[... + 1] += (crms[cls] beta)^2
+    const int32_t* blkslot;
+    double* blkacc;
+    const float* cmax;
+    const float* crms;
+    float lbin0;
+    int nbin;
 };
+
+__device__ __forceinline__ void block_stats(const ExpandArgs& p, float x, int stream, int64_t t0, int ns, int a,
+                                            int c) {
+    if (stream < NCLASS || stream >= 2 * NCLASS) return;   // FP32 quartets only
+    const int slot = __ldg(p.blkslot + t0 + (int64_t)a * ns + c);
+    if (slot < 0) return;
+    const int cls = stream - NCLASS;
+    const int j = min(max((int)floorf(x - p.lbin0), 0), p.nbin - 1);
+    const double beta = (double)exp2f(x);
+    double* acc = p.blkacc + ((int64_t)slot * p.nbin + j) * 2;
+    atomicAdd(acc, (double)__ldg(p.cmax + cls) * beta);
+    const double r = (double)__ldg(p.crms + cls) * beta;
+    atomicAdd(acc + 1, r * r);
+}
 
 __device__ __forceinline__ bool above(float x, float lthr, double thr, const double* __restrict__ snorm,
                                       const double* __restrict__ pnorm, int64_t ab, int64_t bd, int64_t cd) {
@@ -99,8 +124,13 @@ __device__ __forceinline__ int decide(const ExpandArgs& p, float x, float sab, f
         pab = __ldg(p.pairmap + ab);
         pcd = __ldg(p.pairmap + cd);
     }
+    // above the split: FP64, or double-word FP32 where the class has a
+    // double-word kernel; at or below it: FP32
     int prec = 0;
-    if (p.mixed) prec = above(x, p.lsplit, p.split, p.snorm, p.pnorm, ab, bd, cd) ? 0 : 1;
+    if (p.mixed) {
+        if (!above(x, p.lsplit, p.split, p.snorm, p.pnorm, ab, bd, cd)) prec = 1;
+        else if (p.mixed == KX_MIXED_DW && class_l(cls) <= DW_LMAX) prec = 2;
+    }
     return prec * NCLASS + cls;
 }
 
@@ -134,15 +164,19 @@ __device__ __forceinline__ void emit(int stream, int32_t pab, int32_t pcd, int l
     }
 }
 
-template <bool WRITE>
+// MODE 0: count pass; 1: write pass; 2: count pass with the block
+// statistics of split planning
+template <int MODE>
 __global__ void __launch_bounds__(EXP_WARPS * 32)
 k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, unsigned long long* __restrict__ cand,
          const unsigned long long* __restrict__ end, unsigned long long* __restrict__ err) {
+    constexpr bool WRITE = MODE == 1;
+    constexpr bool STATS = MODE == 2;
     // bin[s * gridDim.x + block]: count pass writes the block's count of
     // stream s, the write pass reads the scanned offset
-    __shared__ unsigned int scount[2 * NCLASS];
+    __shared__ unsigned int scount[NSTREAM];
     __shared__ WarpTables tabs[EXP_WARPS];
-    for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x)
+    for (int i = threadIdx.x; i < NSTREAM; i += blockDim.x)
         scount[i] = WRITE ? (unsigned)bin[(int64_t)i * gridDim.x + blockIdx.x] : 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -237,9 +271,11 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const float sab = tb.sab[ia * STAGE + ib], scd = tb.scd[ic * STAGE + id];
                     const float x = sab + tb.pbd[ib * STAGE + id] + scd;
                     const int cls = tb.cab[ia * STAGE + ib] * 9 + tb.ccd[ic * STAGE + id];
-                    if (!(diag && ia > ic))
+                    if (!(diag && ia > ic)) {
                         stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns,
                                                pab, pcd);
+                        if (STATS) block_stats(p, x, stream, t0, ns, a0 + ia, c0 + ic);
+                    }
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err, p.sflops, wsum);
             }
@@ -259,7 +295,10 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                     const float sab = p.slog[t0 + (int64_t)a * ns + b], scd = p.slog[t0 + (int64_t)c * ns + d];
                     const float x = sab + p.plog[t0 + (int64_t)b * ns + d] + scd;
                     const int cls = ((p.tl[a] * 3 + p.tl[b]) * 3 + p.tl[c]) * 3 + p.tl[d];
-                    if (!(diag && a > c)) stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, t0, ns, pab, pcd);
+                    if (!(diag && a > c)) {
+                        stream = decide<WRITE>(p, x, sab, scd, a, b, c, d, cls, t0, ns, pab, pcd);
+                        if (STATS) block_stats(p, x, stream, t0, ns, a, c);
+                    }
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err, p.sflops, wsum);
             }
@@ -271,7 +310,7 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
     }
     if (!WRITE) {
         __syncthreads();
-        for (int i = threadIdx.x; i < 2 * NCLASS; i += blockDim.x)
+        for (int i = threadIdx.x; i < NSTREAM; i += blockDim.x)
             bin[(int64_t)i * gridDim.x + blockIdx.x] = scount[i];
         for (int d = 16; d > 0; d >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, d);
         if (lane == 0 && ncand) atomicAdd(cand, ncand / 32);
@@ -305,6 +344,12 @@ static ExpandArgs make_args(kx_ctx* c, const Task* leaves, int64_t n, double tau
     a.sym = sym;
     a.work = c->work_acc;
     a.sflops = c->d_sflops;
+    a.blkslot = c->plan_slot;
+    a.blkacc = c->plan_acc;
+    a.cmax = c->d_cmax;
+    a.crms = c->d_crms;
+    a.lbin0 = c->plan_lbin0;
+    a.nbin = c->plan_nbin;
     return a;
 }
 
@@ -320,7 +365,11 @@ int expand_count(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
                  int64_t* bin) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<false><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+    if (c->plan_slot)
+        k_expand<2><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+                                                                       nullptr, nullptr);
+    else
+        k_expand<0><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
                                                                        nullptr, nullptr);
     return KX_OK;
 }
@@ -329,7 +378,7 @@ int expand_write(kx_ctx* c, const Task* leaves, int64_t n, double tau, double sp
                  int64_t* bin_off, Quartet* rec) {
     if (n <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, n, tau, split, mixed, shell_screen);
-    k_expand<true><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
+    k_expand<1><<<expand_grid(c, n), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
                                                                       c->d_counters + CTR_END,
                                                                       c->d_counters + CTR_ERR);
     return KX_OK;
@@ -340,7 +389,7 @@ int expand_count_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* 
     if (cap <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, cap, tau, split, mixed, shell_screen);
     a.dn = dn;
-    k_expand<false><<<expand_grid(c, cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
+    k_expand<0><<<expand_grid(c, cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin, nullptr, c->d_counters + CTR_CAND,
                                                                          nullptr, nullptr);
     c->launches++;
     return KX_OK;
@@ -351,7 +400,7 @@ int expand_write_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* 
     if (cap <= 0) return KX_OK;
     ExpandArgs a = make_args(c, leaves, cap, tau, split, mixed, shell_screen);
     a.dn = dn;
-    k_expand<true><<<expand_grid(c, cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
+    k_expand<1><<<expand_grid(c, cap), EXP_WARPS * 32, 0, c->stream>>>(a, bin_off, rec, nullptr,
                                                                         c->d_counters + CTR_END,
                                                                         c->d_counters + CTR_ERR);
     c->launches++;
@@ -362,7 +411,23 @@ int expand_write_dev(kx_ctx* c, const Task* leaves, int64_t cap, const int64_t* 
 // class dispatch
 // ---------------------------------------------------------------------------
 
+EriKern eri_kernel_dw(int cls) {
+    switch (cls / 9) {
+        case 0: return eri_kernel_dw_ab00(cls);
+        case 1: return eri_kernel_dw_ab01(cls);
+        case 2: return eri_kernel_dw_ab02(cls);
+        case 3: return eri_kernel_dw_ab10(cls);
+        case 4: return eri_kernel_dw_ab11(cls);
+        case 5: return eri_kernel_dw_ab12(cls);
+        case 6: return eri_kernel_dw_ab20(cls);
+        case 7: return eri_kernel_dw_ab21(cls);
+        case 8: return eri_kernel_dw_ab22(cls);
+        default: return EriKern{nullptr, 0, 0};
+    }
+}
+
 EriKern eri_kernel(int cls, int prec, int variant) {
+    if (prec == 2) return eri_kernel_dw(cls);
     switch (cls / 9) {
         case 0: return eri_kernel_ab00(cls, prec, variant);
         case 1: return eri_kernel_ab01(cls, prec, variant);
@@ -403,10 +468,17 @@ EriArgs eri_args(kx_ctx* c, int cls, int prec, const Quartet* rec, int64_t i0, i
     a.range = range;
     a.bmeta = c->d_pairmeta[pab];
     a.kmeta = c->d_pairmeta[pcd];
-    a.bra = prec == 0 ? (const void*)c->d_pair64[pab] : (const void*)c->d_pair32[pab];
-    a.ket = prec == 0 ? (const void*)c->d_pair64[pcd] : (const void*)c->d_pair32[pcd];
-    a.boys = prec == 0 ? (const void*)c->d_boys64 : (const void*)c->d_boys32;
-    a.P = prec == 0 ? (const void*)P : (const void*)c->d_P32;
+    if (prec == 2) {
+        a.bra = c->d_pairdw[pab];
+        a.ket = c->d_pairdw[pcd];
+        a.boys = c->d_boysdw;
+        a.P = c->d_Pdw;
+    } else {
+        a.bra = prec == 0 ? (const void*)c->d_pair64[pab] : (const void*)c->d_pair32[pab];
+        a.ket = prec == 0 ? (const void*)c->d_pair64[pcd] : (const void*)c->d_pair32[pcd];
+        a.boys = prec == 0 ? (const void*)c->d_boys64 : (const void*)c->d_boys32;
+        a.P = prec == 0 ? (const void*)P : (const void*)c->d_P32;
+    }
     a.K = K;
     a.nab = c->n_pairs[pab];
     a.ncd = c->n_pairs[pcd];

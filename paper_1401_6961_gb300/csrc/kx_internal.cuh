@@ -23,6 +23,13 @@ namespace kx {
 
 constexpr int LMAX = 2;
 constexpr int NCLASS = 81;          // (la,lb,lc,ld), l <= 2
+// class-kernel streams s = precision * NCLASS + class: precision 0 = FP64,
+// 1 = FP32, 2 = double-word FP32 (KX_MIXED_DW above the split)
+constexpr int NPREC = 3;
+constexpr int NSTREAM = NPREC * NCLASS;
+// double-word kernels exist for the classes with la+lb+lc+ld <= DW_LMAX
+constexpr int DW_LMAX = 5;
+__host__ __device__ constexpr int class_l(int cls) { return cls / 27 + (cls / 9) % 3 + (cls / 3) % 3 + cls % 3; }
 constexpr int NPAIRCLASS = 9;       // (la,lb)
 constexpr int MAX_LEVELS = 32;
 constexpr double PI = 3.14159265358979323846;
@@ -36,7 +43,7 @@ constexpr int BOYS_NPTS = 40 * BOYS_DENS + 2;
 constexpr int CTR_CAND = 8;                        // shell quartets screened
 constexpr int CTR_FILTER = CTR_CAND + 1;           // worklist export count
 constexpr int CTR_END = CTR_FILTER + 1;            // per-stream end offsets
-constexpr int CTR_ERR = CTR_END + 2 * NCLASS;      // write-guard violations
+constexpr int CTR_ERR = CTR_END + NSTREAM;         // write-guard violations
 constexpr int NCOUNTERS = 512;
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
@@ -213,15 +220,18 @@ struct kx_ctx {
     int32_t* d_leaf_lo = nullptr;         // leaves (level depth) as tree ranges
     int32_t* d_leaf_hi = nullptr;
 
-    // device: Boys table
+    // device: Boys table (FP64, FP32 and double-word copies of one table)
     double* d_boys64 = nullptr;
     float* d_boys32 = nullptr;
+    float2* d_boysdw = nullptr;
 
     // device: pair tables, rebuilt per build
     int32_t* d_pairmap = nullptr;         // tree (a,b) -> slot in its class, -1 if absent
     kx::PairMeta* d_pairmeta[kx::NPAIRCLASS] = {};
     double* d_pair64[kx::NPAIRCLASS] = {};
     float* d_pair32[kx::NPAIRCLASS] = {};
+    float2* d_pairdw[kx::NPAIRCLASS] = {};      // the FP64 records as double words (KX_MIXED_DW builds)
+    int64_t pairdw_cap[kx::NPAIRCLASS] = {};
     int64_t pair_cap[kx::NPAIRCLASS] = {};
     int64_t n_pairs[kx::NPAIRCLASS] = {};
 
@@ -243,9 +253,11 @@ struct kx_ctx {
     size_t keep_cap = 0, keep_n = 0;
     bool keep_valid = false;
 
-    // FP32 copy of P for the mixed-precision kernels (ld = n_fn)
+    // FP32 and double-word copies of P for the mixed-precision kernels (same layout as P)
     float* d_P32 = nullptr;
     size_t P32_cap = 0;
+    float2* d_Pdw = nullptr;
+    size_t Pdw_cap = 0;
     // scan temporaries
     int64_t* d_scantmp = nullptr;
     size_t scantmp_cap = 0;
@@ -265,18 +277,18 @@ struct kx_ctx {
     int64_t launches = 0;                 // kernels launched by the current build
     // launch shape of every (precision, class) stream: threads per block and
     // persistent blocks per SM (0 = one thread per record); see kx_autotune
-    int eri_threads[2 * kx::NCLASS] = {};
-    int eri_bpsm[2 * kx::NCLASS] = {};
-    int eri_variant[2 * kx::NCLASS] = {};       // kernel variant of the stream
-    bool eri_smem_set[2 * kx::NCLASS][3] = {};  // dynamic shared memory limit raised, per variant
+    int eri_threads[kx::NSTREAM] = {};
+    int eri_bpsm[kx::NSTREAM] = {};
+    int eri_variant[kx::NSTREAM] = {};       // kernel variant of the stream
+    bool eri_smem_set[kx::NSTREAM][3] = {};  // dynamic shared memory limit raised, per variant
     int n_sm = 0;
-    bool tuned[2 * kx::NCLASS] = {};
+    bool tuned[kx::NSTREAM] = {};
     // what the last eager build saw (sizes for a captured plan)
     int64_t plan_max_rec = 0;             // largest record count of one leaf chunk
     double rec_per_leaf = 48.0;           // shell-quartet records per leaf quartet (last build, with margin):
                                           // sizes the leaf chunks of eager builds
     int64_t last_lq = 1 << 16;            // leaf quartets per chunk of the last eager build
-    uint8_t plan_active[2 * kx::NCLASS] = {};
+    uint8_t plan_active[kx::NSTREAM] = {};
     // autotuning inside an eager build (kx_autotune)
     bool tuning = false;
     double* d_tuneK = nullptr;
@@ -295,11 +307,22 @@ struct kx_ctx {
     int64_t graph_st0 = 0;                // statistics block in d_gw
     cudaStream_t gstream = nullptr;       // capture and replay stream
     // per-stream profile of the last profiled build
-    double prof_ms[2 * kx::NCLASS] = {};
-    int64_t prof_n[2 * kx::NCLASS] = {};
-    double prof_flops[2 * kx::NCLASS] = {};
-    int32_t prof_launches[2 * kx::NCLASS] = {};
+    double prof_ms[kx::NSTREAM] = {};
+    int64_t prof_n[kx::NSTREAM] = {};
+    double prof_flops[kx::NSTREAM] = {};
+    int32_t prof_launches[kx::NSTREAM] = {};
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+    // split planning (kx_split_plan): sampled K shell blocks -> slot (dense
+    // over shell pairs, -1 = not sampled) and their per-bin FP32 sums,
+    // present only during the planning count; per-class error constants
+    int32_t* plan_slot = nullptr;
+    double* plan_acc = nullptr;
+    float plan_lbin0 = 0.f;
+    int plan_nbin = 0;
+    float* d_cmax = nullptr;
+    float* d_crms = nullptr;
+    double graph_split = 0.0;             // split of the captured build (its plan may have chosen it)
+    double graph_err_bound = 0.0, graph_err_est = 0.0;
     // per-row-leaf work of a kx_row_work count (null otherwise) and the
     // FLOPs of one quartet of every stream
     double* work_acc = nullptr;
@@ -349,8 +372,9 @@ int boys_table(kx_ctx* c);                                    // kx_setup.cu
 // P/K addressing of the current build: ldp = ldk = 0 means packed per system
 int set_frames(kx_ctx* c, int64_t ldp, int64_t ldk, bool packed);   // kx_setup.cu
 int p_norms(kx_ctx* c, const double* P);                      // kx_setup.cu
-int pair_tables(kx_ctx* c, double tau, bool want32);          // kx_setup.cu
-int pair_tables_dev(kx_ctx* c, double tau, bool screen);      // kx_setup.cu, capture-safe
+// dw: also fill the double-word copies of the FP64 pair records
+int pair_tables(kx_ctx* c, double tau, bool screen, bool dw);          // kx_setup.cu
+int pair_tables_dev(kx_ctx* c, double tau, bool screen, bool dw);      // kx_setup.cu, capture-safe
 int exclusive_scan(kx_ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host);  // kx_traverse.cu
 // K(mu,nu) = K(nu,mu) wherever the shell of mu comes after the shell of nu
 // in tree order (the half a symmetric build leaves out)
@@ -367,11 +391,14 @@ void drop_graph(kx_ctx* c);
 // captured builds and the launch-shape autotuner (kx_traverse.cu); P and K packed
 int graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double headroom, kx_stats* st);
 int graph_launch(kx_ctx* c, kx_stats* st);
+// split threshold of a mixed build from the FP32 error model (kx_split.cu):
+// fills st->split_used, fp32_err_estimate, fp32_err_bound
+int split_plan(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double budget, kx_stats* st);
 int autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int* n_tuned);
 
 // shell expansion + class kernels (kx_expand.cu, kx_eri_*.cu)
 struct ClassCounts {
-    int64_t n[2 * NCLASS];     // [precision][class]; precision 0 = FP64
+    int64_t n[NSTREAM];        // [precision][class]; precision 0 = FP64
 };
 // Shell-screen passes over a list of leaf quartets.  expand_count writes
 // the number of kept quartets of every (stream, block) into bin[stream *
@@ -424,6 +451,17 @@ struct EriKern {
 };
 
 EriKern eri_kernel(int cls, int prec, int variant);   // kx_expand.cu, over the nine below
+// double-word kernels of the classes with la+lb+lc+ld <= DW_LMAX (else null)
+EriKern eri_kernel_dw(int cls);                       // kx_expand.cu, over the nine below
+EriKern eri_kernel_dw_ab00(int cls);
+EriKern eri_kernel_dw_ab01(int cls);
+EriKern eri_kernel_dw_ab02(int cls);
+EriKern eri_kernel_dw_ab10(int cls);
+EriKern eri_kernel_dw_ab11(int cls);
+EriKern eri_kernel_dw_ab12(int cls);
+EriKern eri_kernel_dw_ab20(int cls);
+EriKern eri_kernel_dw_ab21(int cls);
+EriKern eri_kernel_dw_ab22(int cls);
 // the ket-pruned FP64 and FP32 kernels of a class with la+lb+lc+ld >= 7
 EriKern eri_kernel_big64p(int cls);
 EriKern eri_kernel_bigp(int cls);

@@ -441,7 +441,7 @@ int kx_evaluate_kept(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, 
     if (!c) return KX_EINVAL;
     if (!P || !K || !o) return set_err(c, KX_EINVAL, "null argument");
     if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
-    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision < KX_FP64 || o->precision > KX_MIXED_DW) return set_err(c, KX_EINVAL, "bad precision");
     if (!c->keep_valid) return set_err(c, KX_ESTATE, "no kept leaf list (kx_traverse first)");
     Guard g(c->device);
     if (!g.ok) return set_err(c, KX_ECUDA, "cudaSetDevice failed");
@@ -459,7 +459,7 @@ int kx_exchange_leaves(kx_ctx* c, const double* P, int64_t ldp, const int32_t* l
     if (!c) return KX_EINVAL;
     if (!P || !K || !o || (n > 0 && !leaves) || n < 0) return set_err(c, KX_EINVAL, "bad argument");
     if (ldp < c->n_fn || ldk < c->n_fn) return set_err(c, KX_EINVAL, "leading dimension smaller than n_fn");
-    if (o->precision != KX_FP64 && o->precision != KX_MIXED) return set_err(c, KX_EINVAL, "bad precision");
+    if (o->precision < KX_FP64 || o->precision > KX_MIXED_DW) return set_err(c, KX_EINVAL, "bad precision");
     if (!c->have_tree) return set_err(c, KX_ESTATE, "kx_build_tree must come first");
     const int nl = c->levels[c->depth].n;
     std::vector<Task> h(n);

@@ -777,7 +777,7 @@ int p_norms(kx_ctx* c, const double* P) {
 // F_m(T_i), T_i = i / BOYS_DENS, m = 0..BOYS_M: the top order from its
 // positive-term series e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)),
 // the rest by downward recursion F_{m-1} = (2T F_m + e^{-T}) / (2m-1).
-__global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32, int npts) {
+__global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32, float2* __restrict__ tdw, int npts) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
     double T = (double)i / BOYS_DENS;
@@ -798,6 +798,8 @@ __global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32, 
     for (int m = 0; m <= M; ++m) {
         t64[(int64_t)i * (BOYS_M + 1) + m] = F[m];
         t32[(int64_t)i * BOYS32_ROW + m] = (float)F[m];
+        const float hi = (float)F[m];
+        tdw[(int64_t)i * (BOYS_M + 1) + m] = make_float2(hi, (float)(F[m] - (double)hi));
     }
     for (int m = M + 1; m < BOYS32_ROW; ++m) t32[(int64_t)i * BOYS32_ROW + m] = 0.f;
 }
@@ -806,8 +808,9 @@ int boys_table(kx_ctx* c) {
     int npts = BOYS_NPTS;
     cudaError_t e = cudaMalloc(&c->d_boys64, sizeof(double) * npts * (BOYS_M + 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_boys32, sizeof(float) * npts * BOYS32_ROW);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_boysdw, sizeof(float2) * npts * (BOYS_M + 1));
     if (e != cudaSuccess) return cuda_check(c, e, "boys alloc");
-    k_boys_table<<<(npts + 127) / 128, 128, 0, c->stream>>>(c->d_boys64, c->d_boys32, npts);
+    k_boys_table<<<(npts + 127) / 128, 128, 0, c->stream>>>(c->d_boys64, c->d_boys32, c->d_boysdw, npts);
     return KX_OK;
 }
 
@@ -841,7 +844,8 @@ __global__ void k_pair_fill(const Seg* __restrict__ seg, int nseg, int64_t n2, i
                             const double* __restrict__ talpha, const int32_t* __restrict__ tfoff,
                             const MatFrame* __restrict__ mf, const int64_t* __restrict__ flag,
                             const int64_t* __restrict__ slot, int32_t* __restrict__ pairmap,
-                            PairMeta* __restrict__ meta, double* __restrict__ d64, float* __restrict__ d32) {
+                            PairMeta* __restrict__ meta, double* __restrict__ d64, float* __restrict__ d32,
+                            float2* __restrict__ ddw) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n2) return;
     const int y = seg_find(seg, nseg, i);
@@ -885,6 +889,15 @@ __global__ void k_pair_fill(const Seg* __restrict__ seg, int nseg, int64_t n2, i
     o32[P32_KAB] = (float)o[4];
     o32[15] = 0.f;
     if (stride > 5 + 3 * et) o[stride - 1] = 0.0;
+    // the same record as double words (hi = nearest float, lo = remainder)
+    if (ddw) {
+        float2* od = ddw + s * stride;
+        for (int k = 0; k < stride; ++k) {
+            const double x = o[k];
+            const float hi = (float)x;
+            od[k] = make_float2(hi, (float)(x - (double)hi));
+        }
+    }
 }
 
 __global__ void k_max_reduce(const double* __restrict__ x, int64_t n, unsigned long long* __restrict__ out) {
@@ -905,7 +918,19 @@ static void pair_maxima(kx_ctx* c) {
     c->launches += 2;
 }
 
-int pair_tables(kx_ctx* c, double tau, bool screen) {
+// the double-word pair records of class cls, at the capacity of the FP64 table
+static int reserve_pairdw(kx_ctx* c, int cls) {
+    if (c->pairdw_cap[cls] >= c->pair_cap[cls] && c->d_pairdw[cls]) return KX_OK;
+    cudaFree(c->d_pairdw[cls]);
+    c->d_pairdw[cls] = nullptr;
+    c->pairdw_cap[cls] = 0;
+    const int stride = pair_stride(cls / 3, cls % 3);
+    KX_CUDA(c, cudaMalloc(&c->d_pairdw[cls], sizeof(float2) * stride * std::max<int64_t>(c->pair_cap[cls], 1)));
+    c->pairdw_cap[cls] = c->pair_cap[cls];
+    return KX_OK;
+}
+
+int pair_tables(kx_ctx* c, double tau, bool screen, bool dw) {
     int64_t n2 = c->sp_total;
     pair_maxima(c);
     if (!c->d_pairmap) KX_CUDA(c, cudaMalloc(&c->d_pairmap, sizeof(int32_t) * n2));
@@ -935,9 +960,10 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
             }
             c->pair_cap[cls] = (int64_t)cap;
         }
+        if (dw) KX_TRY(reserve_pairdw(c, cls));
         k_pair_fill<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, cls, c->d_tl, c->d_tctr, c->d_talpha,
                                               c->d_tfoff, c->d_mframe, flag, slot, c->d_pairmap, c->d_pairmeta[cls],
-                                              c->d_pair64[cls], c->d_pair32[cls]);
+                                              c->d_pair64[cls], c->d_pair32[cls], dw ? c->d_pairdw[cls] : nullptr);
         c->launches += 2;
     }
     return KX_OK;
@@ -946,7 +972,7 @@ int pair_tables(kx_ctx* c, double tau, bool screen) {
 // Capture-safe: no host read-back.  The tables must already hold every pair
 // of nonzero Schwarz factor (pair_tables(c, 0, false) reserves that); the
 // slot bound of the class kernels is then the capacity.
-int pair_tables_dev(kx_ctx* c, double tau, bool screen) {
+int pair_tables_dev(kx_ctx* c, double tau, bool screen, bool dw) {
     int64_t n2 = c->sp_total;
     if (!c->d_pairmap || c->scan_cap < (size_t)2 * n2 + 16)
         return set_err(c, KX_ESTATE, "pair tables not reserved");
@@ -959,9 +985,11 @@ int pair_tables_dev(kx_ctx* c, double tau, bool screen) {
                                                c->d_counters, screen ? 1 : 0, cls, flag);
         KX_TRY(exclusive_scan_dev(c, flag, slot, n2, nullptr, (int64_t*)(c->d_counters + 2)));
         c->n_pairs[cls] = c->pair_cap[cls];
+        if (dw && (c->pairdw_cap[cls] < c->pair_cap[cls] || !c->d_pairdw[cls]))
+            return set_err(c, KX_ESTATE, "double-word pair tables not reserved");
         k_pair_fill<<<g, 256, 0, c->stream>>>(c->d_sseg, c->n_sys, n2, cls, c->d_tl, c->d_tctr, c->d_talpha,
                                               c->d_tfoff, c->d_mframe, flag, slot, c->d_pairmap, c->d_pairmeta[cls],
-                                              c->d_pair64[cls], c->d_pair32[cls]);
+                                              c->d_pair64[cls], c->d_pair32[cls], dw ? c->d_pairdw[cls] : nullptr);
         c->launches += 2;
     }
     return KX_OK;

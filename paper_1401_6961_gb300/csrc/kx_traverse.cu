@@ -224,6 +224,18 @@ __global__ void k_to_f32(const double* __restrict__ P, int64_t ldp, int64_t rows
     }
 }
 
+// double-word copy of P (hi = nearest float, lo = the rounded remainder)
+__global__ void k_to_dw(const double* __restrict__ P, int64_t ldp, int64_t rows, int64_t n,
+                        float2* __restrict__ Pdw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (i / n) * ldp + (i % n);
+        const double x = P[j];
+        const float hi = __double2float_rn(x);
+        Pdw[j] = make_float2(hi, __double2float_rn(x - (double)hi));
+    }
+}
+
 // ===========================================================================
 // driver
 // ===========================================================================
@@ -350,15 +362,26 @@ int tune_stream(kx_ctx* c, int s, const Quartet* rec, int64_t i0, int64_t i1, co
     return KX_OK;
 }
 
+// adds n shell quartets of stream s to the build's counters
+void add_stream_stats(kx_stats* st, int s, int64_t n) {
+    const double f = class_flops(s % NCLASS) * (double)n;
+    st->n_shell_quartets += n;
+    switch (s / NCLASS) {
+        case 0: st->flops_fp64 += f; st->n_shell_quartets_fp64 += n; break;
+        case 1: st->flops_fp32 += f; break;
+        default: st->flops_dw += f; st->n_shell_quartets_dw += n; break;
+    }
+}
+
 // shell screen, class binning and class kernels for one list of leaf quartets
 int process_leaves(Run& r, const Task* leaves, int64_t n) {
     kx_ctx* c = r.c;
     if (n <= 0) return KX_OK;
-    const int mixed = r.o->precision == KX_MIXED;
+    const int mixed = r.o->precision;
     const double split = mixed ? r.o->split_threshold : 0.0;
     r.tm->mark(ST_EXPAND);
     const unsigned nb = expand_blocks(c, n);
-    const int64_t nbin = (int64_t)2 * NCLASS * nb;
+    const int64_t nbin = (int64_t)NSTREAM * nb;
     KX_TRY(grow(c, &c->d_bin, &c->bin_cap, (size_t)(2 * nbin)));
     int64_t* bin = c->d_bin;
     int64_t* binoff = c->d_bin + nbin;
@@ -379,24 +402,21 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     }
     if (total == 0) return KX_OK;
     // stream s starts at binoff[s * nb]
-    int64_t off[2 * NCLASS + 1];
-    KX_CUDA(c, cudaMemcpy2DAsync(off, sizeof(int64_t), binoff, sizeof(int64_t) * nb, sizeof(int64_t), 2 * NCLASS,
+    int64_t off[NSTREAM + 1];
+    KX_CUDA(c, cudaMemcpy2DAsync(off, sizeof(int64_t), binoff, sizeof(int64_t) * nb, sizeof(int64_t), NSTREAM,
                                  cudaMemcpyDeviceToHost, c->stream));
     KX_CUDA(c, cudaStreamSynchronize(c->stream));
-    off[2 * NCLASS] = total;
-    unsigned long long h[2 * NCLASS], endv[2 * NCLASS];
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    off[NSTREAM] = total;
+    unsigned long long h[NSTREAM], endv[NSTREAM];
+    for (int s = 0; s < NSTREAM; ++s) {
         h[s] = (unsigned long long)(off[s + 1] - off[s]);
         endv[s] = (unsigned long long)off[s + 1];
     }
     if (r.count_only) {
-        for (int s = 0; s < 2 * NCLASS; ++s) {
-            const double f = class_flops(s % NCLASS) * (double)h[s];
-            if (s < NCLASS) r.st->flops_fp64 += f; else r.st->flops_fp32 += f;
+        for (int s = 0; s < NSTREAM; ++s) {
+            add_stream_stats(r.st, s, (int64_t)h[s]);
             c->prof_n[s] += (int64_t)h[s];
         }
-        r.st->n_shell_quartets += total;
-        for (int s = 0; s < NCLASS; ++s) r.st->n_shell_quartets_fp64 += (int64_t)h[s];
         r.st->n_chunks++;
         return KX_OK;
     }
@@ -405,7 +425,7 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
     KX_TRY(expand_write(c, leaves, n, r.o->tau, split, mixed, r.o->shell_screen, binoff, c->d_rec));
     c->launches++;
     r.tm->mark(ST_ERI);
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    for (int s = 0; s < NSTREAM; ++s) {
         if (!h[s]) continue;
         const int prec = s / NCLASS, cls = s % NCLASS;
         c->plan_active[s] = 1;
@@ -422,14 +442,11 @@ int process_leaves(Run& r, const Task* leaves, int64_t n) {
             c->prof_ev.push_back({s, {e0, e1}});
         }
         c->launches++;
-        const double f = class_flops(cls) * (double)h[s];
-        if (prec == 0) r.st->flops_fp64 += f; else r.st->flops_fp32 += f;
+        add_stream_stats(r.st, s, (int64_t)h[s]);
         c->prof_n[s] += (int64_t)h[s];
-        c->prof_flops[s] += f;
+        c->prof_flops[s] += class_flops(cls) * (double)h[s];
         c->prof_launches[s] += 1;
     }
-    r.st->n_shell_quartets += total;
-    for (int s = 0; s < NCLASS; ++s) r.st->n_shell_quartets_fp64 += (int64_t)h[s];
     r.st->n_chunks++;
     KX_CUDA(c, cudaGetLastError());
     return KX_OK;
@@ -509,7 +526,7 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
 
     c->launches = 0;
     c->plan_max_rec = 0;
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    for (int s = 0; s < NSTREAM; ++s) {
         c->plan_active[s] = 0;
         c->prof_ms[s] = 0.0;
         c->prof_n[s] = 0;
@@ -534,13 +551,18 @@ int drive(kx_ctx* c, int mode, const double* P, int64_t ldp, const kx_opts* o, d
             KX_CUDA(c, cudaMemset2DAsync(K, sizeof(double) * ldk, 0, sizeof(double) * c->n_fn, c->n_fn, c->stream));
     }
     KX_TRY(p_norms(c, P));
-    if (evaluate && o->precision == KX_MIXED) {
+    if (evaluate && o->precision != KX_FP64) {
         const int64_t rows = packed ? 1 : c->n_fn, cols = packed ? mat_total : c->n_fn, ld = packed ? 0 : ldp;
         KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)((rows - 1) * ld + cols)));
         k_to_f32<<<1024, 256, 0, c->stream>>>(P, ld, rows, cols, c->d_P32);
         c->launches++;
+        if (o->precision == KX_MIXED_DW) {
+            KX_TRY(grow(c, &c->d_Pdw, &c->Pdw_cap, (size_t)((rows - 1) * ld + cols)));
+            k_to_dw<<<1024, 256, 0, c->stream>>>(P, ld, rows, cols, c->d_Pdw);
+            c->launches++;
+        }
     }
-    if (evaluate) KX_TRY(pair_tables(c, o->tau, o->shell_screen != 0));
+    if (evaluate) KX_TRY(pair_tables(c, o->tau, o->shell_screen != 0, o->precision == KX_MIXED_DW));
     const bool keep = mode == RUN_TRAVERSE || (mode == RUN_EXCHANGE && o->keep_worklist);
     if (mode == RUN_EXCHANGE || mode == RUN_TRAVERSE) {
         c->keep_n = 0;
@@ -719,11 +741,11 @@ struct GraphWords {
     int64_t t(int k) const { return 32 + k; }               // level totals (scan grands) [D + 1]
     int64_t wr(int k) const { return 64 + 3 * k; }          // write ranges of levels [D]
     int64_t ch(int j) const { return 160 + 4 * (int64_t)j; } // chunk: p0, p1, o0, n_leaf
-    int64_t rg() const { return 160 + 4 * (int64_t)nch; }   // stream ranges [2 * 162]
-    int64_t ne() const { return rg() + 4 * NCLASS; }        // leaf count of the write pass
+    int64_t rg() const { return 160 + 4 * (int64_t)nch; }   // stream ranges [2 * NSTREAM]
+    int64_t ne() const { return rg() + 2 * NSTREAM; }       // leaf count of the write pass
     int64_t bt() const { return ne() + 1; }                 // record total of a chunk
-    int64_t st() const { return bt() + 1; }                 // statistics: records per stream [162]
-    int64_t lq() const { return st() + 2 * NCLASS; }        // leaf quartets evaluated
+    int64_t st() const { return bt() + 1; }                 // statistics: records per stream [NSTREAM]
+    int64_t lq() const { return st() + NSTREAM; }        // leaf quartets evaluated
     int64_t flag() const { return lq() + 1; }               // overflow
     int64_t size() const { return flag() + 3; }             // + two read-back slots
 };
@@ -778,13 +800,13 @@ __global__ void k_stream_setup(const int64_t* __restrict__ binoff, int nb, const
                                int64_t* __restrict__ flag) {
     const int64_t tot = *total;
     bool ok = tot <= rec_cap;
-    for (int s = threadIdx.x; s < 2 * NCLASS; s += blockDim.x) {
-        const int64_t a = binoff[(int64_t)s * nb], b = s + 1 < 2 * NCLASS ? binoff[(int64_t)(s + 1) * nb] : tot;
+    for (int s = threadIdx.x; s < NSTREAM; s += blockDim.x) {
+        const int64_t a = binoff[(int64_t)s * nb], b = s + 1 < NSTREAM ? binoff[(int64_t)(s + 1) * nb] : tot;
         if (b > a && !active[s]) ok = false;
     }
     ok = __syncthreads_and(ok);
-    for (int s = threadIdx.x; s < 2 * NCLASS; s += blockDim.x) {
-        const int64_t a = binoff[(int64_t)s * nb], b = s + 1 < 2 * NCLASS ? binoff[(int64_t)(s + 1) * nb] : tot;
+    for (int s = threadIdx.x; s < NSTREAM; s += blockDim.x) {
+        const int64_t a = binoff[(int64_t)s * nb], b = s + 1 < NSTREAM ? binoff[(int64_t)(s + 1) * nb] : tot;
         ranges[2 * s] = ok ? a : 0;
         ranges[2 * s + 1] = ok ? b : 0;
         end[s] = ok ? (unsigned long long)b : 0ull;
@@ -804,10 +826,10 @@ struct GraphCaps {
 // the screen, binning and class launches of one leaf list (capture-safe)
 int chunk_dev(kx_ctx* c, const kx_opts* o, const GraphWords& W, const GraphCaps& cap, const Task* leaves,
               int64_t leaf_cap, const int64_t* dn, const double* P, double* K) {
-    const int mixed = o->precision == KX_MIXED;
+    const int mixed = o->precision;
     const double split = mixed ? o->split_threshold : 0.0;
     const unsigned nb = expand_blocks(c, leaf_cap);
-    const int64_t nbin = (int64_t)2 * NCLASS * nb;
+    const int64_t nbin = (int64_t)NSTREAM * nb;
     int64_t* bin = c->d_bin;
     int64_t* binoff = c->d_bin + nbin;
     int64_t* w = c->d_gw;
@@ -819,7 +841,7 @@ int chunk_dev(kx_ctx* c, const kx_opts* o, const GraphWords& W, const GraphCaps&
     c->launches++;
     KX_TRY(expand_write_dev(c, leaves, leaf_cap, w + W.ne(), o->tau, split, mixed, o->shell_screen, binoff,
                             c->d_rec));
-    for (int s = 0; s < 2 * NCLASS; ++s) {
+    for (int s = 0; s < NSTREAM; ++s) {
         if (!c->plan_active[s]) continue;
         KX_TRY(eri_launch(c, s % NCLASS, s / NCLASS, c->d_rec, 0, 0, w + W.rg() + 2 * s, P, K));
         c->launches++;
@@ -840,11 +862,15 @@ int capture_build(kx_ctx* c, const double* P, const kx_opts* o, double* K, const
     KX_CUDA(c, cudaMemsetAsync(c->d_counters + CTR_ERR, 0, sizeof(unsigned long long), c->stream));
     KX_CUDA(c, cudaMemsetAsync(K, 0, sizeof(double) * mat_total, c->stream));
     KX_TRY(p_norms(c, P));
-    if (o->precision == KX_MIXED) {
+    if (o->precision != KX_FP64) {
         k_to_f32<<<1024, 256, 0, c->stream>>>(P, 0, 1, mat_total, c->d_P32);
         c->launches++;
     }
-    KX_TRY(pair_tables_dev(c, o->tau, o->shell_screen != 0));
+    if (o->precision == KX_MIXED_DW) {
+        k_to_dw<<<1024, 256, 0, c->stream>>>(P, 0, 1, mat_total, c->d_Pdw);
+        c->launches++;
+    }
+    KX_TRY(pair_tables_dev(c, o->tau, o->shell_screen != 0, o->precision == KX_MIXED_DW));
     const double* S = c->d_nrm_s;
     const double* Pn = c->d_nrm_p;
     if (D == 0) {
@@ -905,7 +931,7 @@ int capture_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, const 
     const int D = c->depth, ny = c->n_sys;
     GraphWords W{D, (int)cap.nch};
     const unsigned nb = expand_blocks(c, cap.lq + 16);
-    const int64_t nbin = (int64_t)2 * NCLASS * nb;
+    const int64_t nbin = (int64_t)NSTREAM * nb;
     const int64_t fcap = std::max<int64_t>({cap.fcap, cap.lq + 16, (int64_t)ny + 16});
     KX_TRY(grow(c, &c->d_front[0], &c->front_cap[0], (size_t)fcap));
     KX_TRY(grow(c, &c->d_front[1], &c->front_cap[1], (size_t)fcap));
@@ -915,7 +941,8 @@ int capture_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, const 
     KX_TRY(grow(c, &c->d_rec, &c->rec_cap, (size_t)cap.rec));
     KX_TRY(grow(c, &c->d_scantmp, &c->scantmp_cap,
                 scan_scratch(std::max<int64_t>({cap.mcap, nbin, c->sp_total}))));
-    if (o->precision == KX_MIXED) KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)c->sys_mat[ny]));
+    if (o->precision != KX_FP64) KX_TRY(grow(c, &c->d_P32, &c->P32_cap, (size_t)c->sys_mat[ny]));
+    if (o->precision == KX_MIXED_DW) KX_TRY(grow(c, &c->d_Pdw, &c->Pdw_cap, (size_t)c->sys_mat[ny]));
     if (c->gw_n < (size_t)W.size()) {
         cudaFree(c->d_gw);
         cudaFreeHost(c->h_gw);
@@ -926,7 +953,7 @@ int capture_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, const 
         KX_CUDA(c, cudaMallocHost(&c->h_gw, sizeof(int64_t) * W.size()));
         c->gw_n = (size_t)W.size();
     }
-    if (!c->d_gactive) KX_CUDA(c, cudaMalloc(&c->d_gactive, 2 * NCLASS));
+    if (!c->d_gactive) KX_CUDA(c, cudaMalloc(&c->d_gactive, NSTREAM));
     cudaFree(c->d_groots);
     c->d_groots = nullptr;
     KX_CUDA(c, cudaMalloc(&c->d_groots, sizeof(Task) * ny));
@@ -937,7 +964,7 @@ int capture_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, const 
         n0[0] = ny;
         KX_CUDA(c, cudaMemcpy(c->d_groots, roots.data(), sizeof(Task) * ny, cudaMemcpyHostToDevice));
         KX_CUDA(c, cudaMemcpy(c->d_gw, n0.data(), sizeof(int64_t) * 32, cudaMemcpyHostToDevice));
-        KX_CUDA(c, cudaMemcpy(c->d_gactive, c->plan_active, 2 * NCLASS, cudaMemcpyHostToDevice));
+        KX_CUDA(c, cudaMemcpy(c->d_gactive, c->plan_active, NSTREAM, cudaMemcpyHostToDevice));
     }
     KX_TRY(set_frames(c, 0, 0, true));
     if (!c->gstream) KX_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
@@ -1004,7 +1031,8 @@ int graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double h
         cap.lq = std::max<int64_t>(1 << 16, (int64_t)(cap.lq * (double)budget / need * 0.8));
         cap.rec = budget;
     }
-    KX_TRY(pair_tables(c, 0.0, false));   // reserve every pair of nonzero Schwarz factor
+    // reserve every pair of nonzero Schwarz factor
+    KX_TRY(pair_tables(c, 0.0, false, o->precision == KX_MIXED_DW));
     for (int attempt = 0; attempt < 4; ++attempt) {
         cap.nch = std::max<int64_t>(1, (int64_t)std::ceil(st->n_tasks[D] * m / (double)cap.lq));
         if (cap.nch > 4096) return set_err(c, KX_ECAPACITY, "too many leaf chunks for a captured build");
@@ -1022,8 +1050,8 @@ int graph_plan(kx_ctx* c, const double* P, const kx_opts* o, double* K, double h
 
 int graph_launch(kx_ctx* c, kx_stats* st) {
     if (!c->graph_valid) return set_err(c, KX_ESTATE, "no captured build (kx_graph_plan)");
-    // statistics block: records per stream [162], leaf quartets, overflow
-    const int64_t nstat = 2 * NCLASS + 2;
+    // statistics block: records per stream [NSTREAM], leaf quartets, overflow
+    const int64_t nstat = NSTREAM + 2;
     const int64_t st0 = c->graph_st0;
     // the graph runs on the context's capture stream, ordered after and
     // before the work of the context's own stream
@@ -1054,32 +1082,28 @@ int graph_launch(kx_ctx* c, kx_stats* st) {
         const int D = c->graph_depth;
         for (int k = 0; k <= D && k < 32; ++k) st->n_tasks[k] = k == 0 ? c->h_gw[0] : c->h_gw[32 + k];
         st->depth = D;
-        for (int s = 0; s < 2 * NCLASS; ++s) {
-            st->n_shell_quartets += c->h_gw[st0 + s];
-            if (s < NCLASS) st->n_shell_quartets_fp64 += c->h_gw[st0 + s];
-        }
-        st->n_leaf_quartets = c->h_gw[st0 + 2 * NCLASS];
+        for (int s = 0; s < NSTREAM; ++s) add_stream_stats(st, s, c->h_gw[st0 + s]);
+        st->n_leaf_quartets = c->h_gw[st0 + NSTREAM];
         st->n_candidates = (int64_t)cand;
         st->n_launches = (int32_t)c->graph_launches;
         st->ms_total = ms;
-        for (int s = 0; s < 2 * NCLASS; ++s) {
-            const double f = class_flops(s % NCLASS) * (double)c->h_gw[st0 + s];
-            if (s < NCLASS) st->flops_fp64 += f; else st->flops_fp32 += f;
-        }
+        st->split_used = c->graph_split;
+        st->fp32_err_estimate = c->graph_err_est;
+        st->fp32_err_bound = c->graph_err_bound;
     }
-    if (c->h_gw[st0 + 2 * NCLASS + 1]) return set_err(c, KX_ECAPACITY, "a count exceeded the captured plan: re-plan");
+    if (c->h_gw[st0 + NSTREAM + 1]) return set_err(c, KX_ECAPACITY, "a count exceeded the captured plan: re-plan");
     if (werr) return set_err(c, KX_ECUDA, "shell-quartet count and write passes disagree");
     return KX_OK;
 }
 
 int autotune(kx_ctx* c, const double* P, const kx_opts* o, double* K, kx_stats* st, int* n_tuned) {
     KX_TRY(grow(c, &c->d_tuneK, &c->tuneK_cap, (size_t)c->sys_mat[c->n_sys]));
-    for (int s = 0; s < 2 * NCLASS; ++s) c->tuned[s] = false;
+    for (int s = 0; s < NSTREAM; ++s) c->tuned[s] = false;
     c->tuning = true;
     int r = drive(c, RUN_EXCHANGE, P, 0, o, K, 0, st, nullptr, 0);
     c->tuning = false;
     int n = 0;
-    for (int s = 0; s < 2 * NCLASS; ++s) n += c->tuned[s];
+    for (int s = 0; s < NSTREAM; ++s) n += c->tuned[s];
     if (n_tuned) *n_tuned = n;
     return r;
 }

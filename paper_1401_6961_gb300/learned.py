@@ -125,6 +125,11 @@ class Model:
     params: np.ndarray        # (NP,) float32
     residual_std: float       # std of (prediction - target) on the training traces
     losses: List[float]
+    # decades added to every prediction by the cull: the q-quantile of
+    # (target - prediction) on traces of systems kept out of training
+    # (calibrate); None = margin * residual_std
+    margin: Optional[float] = None
+    margin_q: Optional[float] = None
 
 
 def train(tr: Traces, epochs: int = 400, lr: float = 3e-3, batch: int = 8192, seed: int = 0,
@@ -162,6 +167,19 @@ def train(tr: Traces, epochs: int = 400, lr: float = 3e-3, batch: int = 8192, se
     return Model(prm.cpu().numpy(), float(res.std().item()), losses)
 
 
+def calibrate(model: Model, held_out: Traces, q: float = 0.999, device: int = 0) -> Model:
+    """The same network with its cull margin set from held-out traces: the
+    q-quantile of how far the true log10 contribution lies above the BF16
+    prediction, over systems of a family the network was not trained on (a
+    distribution-free margin, unlike the Gaussian residual_std)."""
+    torch = _torch()
+    dev = torch.device("cuda", device)
+    X = torch.from_numpy(np.ascontiguousarray(held_out.features)).to(dev)
+    pred = predict(model.params, X, device).cpu().numpy().astype(np.float64)
+    under = held_out.targets.astype(np.float64) - pred
+    return dataclasses.replace(model, margin=max(0.0, float(np.quantile(under, q))), margin_q=q)
+
+
 def predict(params, X, device: int = 0):
     """BF16 inference of the network on device features X (n, 10)."""
     torch = _torch()
@@ -179,10 +197,11 @@ def learned_exchange(ex, P, model: Model, tau: float, budget: Optional[float] = 
     then the ERI stage over what remains.  Returns (K, info).
 
     A leaf quartet of bound <= 10 tau is dropped when its predicted
-    contribution, raised by ``margin`` residual standard deviations and
-    multiplied by the square root of the number of such quartets in its K
-    block, is below ``budget`` (default tau / 10): the predicted
-    root-sum-square of what any K block loses stays below the budget."""
+    contribution, raised by the model's calibrated margin (else by
+    ``margin`` residual standard deviations) and multiplied by the square
+    root of the number of such quartets in its K block, is below ``budget``
+    (default tau / 10): the predicted root-sum-square of what any K block
+    loses stays below the budget."""
     torch = _torch()
     ctx = ex.ctx
     o = B.kx_default_opts(tau=tau, **opts)
@@ -192,8 +211,9 @@ def learned_exchange(ex, P, model: Model, tau: float, budget: Optional[float] = 
         B.kx_leaf_features(ctx, feat.data_ptr(), n)
     pred = predict(model.params, feat[:n], ex.device) if n else feat[:0, 0]
     lb = math.log10(0.1 * tau if budget is None else budget)
-    # the margin shifts every prediction up: pred + margin * sigma + log10(m)/2 < log10(budget)
-    kept = B.kx_cull_kept(ctx, pred.data_ptr(), tau, lb - margin * model.residual_std) if n else 0
+    # the margin shifts every prediction up: pred + margin + log10(m)/2 < log10(budget)
+    shift = model.margin if model.margin is not None else margin * model.residual_std
+    kept = B.kx_cull_kept(ctx, pred.data_ptr(), tau, lb - shift) if n else 0
     if K is None:
         K = torch.empty_like(P)
     st = B.kx_evaluate_kept(ctx, P.data_ptr(), P.stride(0), o, K.data_ptr(), K.stride(0))

@@ -50,8 +50,8 @@ def test_struct_layouts_match_header(lib):
     import paper_1401_6961_gb300 as kx
     assert ctypes.sizeof(kx.kx_opts) == 64
     assert ctypes.sizeof(kx.kx_basis) == 40
-    # 4 counters + 32 levels + 4 ints + 11 doubles
-    assert ctypes.sizeof(kx.kx_stats) == 8 * 4 + 8 * 32 + 4 * 4 + 8 * 11
+    # 5 counters + 32 levels + 4 ints + 12 doubles
+    assert ctypes.sizeof(kx.kx_stats) == 8 * 5 + 8 * 32 + 4 * 4 + 8 * 12
 
 
 def test_create_rejects_bad_basis_without_gpu(lib):

@@ -36,7 +36,7 @@ class _FakeKx:
 
 
 def test_kernel_names_follow_the_variant_of_each_stream():
-    v = np.zeros(162, dtype=np.int32)
+    v = np.zeros(243, dtype=np.int32)
     dd = 80                                 # (dd|dd)
     assert bench.kernel_name(_FakeKx(v), None, 40) == "k_eri<1,1,1,1,double>"
     assert bench.kernel_name(_FakeKx(v), None, 81 + 40) == "k_eri<1,1,1,1,float>"
@@ -48,6 +48,7 @@ def test_kernel_names_follow_the_variant_of_each_stream():
     assert bench.kernel_name(_FakeKx(v), None, 81 + dd) == "k_eri_big<2,2,2,2>"
     v[81 + dd] = 1
     assert bench.kernel_name(_FakeKx(v), None, 81 + dd) == "k_eri_bigp<2,2,2,2>"
+    assert bench.kernel_name(_FakeKx(v), None, 162 + 40) == "k_eri<1,1,1,1,kx::dw>"
 
 
 def test_workload_descriptions():

@@ -15,7 +15,9 @@ with the oracle's direct exchange.
 Tolerances: FP64, the contract's absolute 1e-10.  Forced FP32 (split above
 every bound): 16 eps32 beta with beta = S_ab ||P_bd||_F S_cd, the Eq. 8
 bound of the quartet; single FP32 quartets measured on GB300 stay below
-6.2 eps32 beta in every class.
+6.2 eps32 beta in every class.  Double-word FP32 (KX_MIXED_DW with split 0:
+every class with la+lb+lc+ld <= 5 in double words, the rest in FP64): the
+FP64 bar, 1e-10.
 """
 import numpy as np
 import pytest
@@ -77,9 +79,19 @@ def run_case(kx, T, precision):
         opts = dict(tau=0.0, symmetric=0)
         if precision == "fp32":
             opts.update(precision=kx.KX_MIXED, split_threshold=1e300)
+        elif precision == "dw":
+            opts.update(precision=kx.KX_MIXED_DW, split_threshold=0.0)
         K = ex(torch.from_numpy(P).cuda(), **opts).cpu().numpy()
         if precision == "fp32":
             assert ex.stats.n_shell_quartets_fp64 == 0
+        elif precision == "dw":
+            # the quartet of the class itself runs in double words when L <= 5,
+            # in FP64 above; nothing runs in FP32 at split 0
+            if la + lb + lc + ld <= 5:
+                assert ex.stats.n_shell_quartets_dw >= 1
+            else:
+                assert ex.stats.n_shell_quartets_fp64 >= 1
+            assert ex.stats.n_shell_quartets == ex.stats.n_shell_quartets_dw + ex.stats.n_shell_quartets_fp64
         ex.close()
         ctr = s.xyz[s.shell_atom]
         v = oracle.eri(ctr[0], ALPHA[0], la, ctr[1], ALPHA[1], lb, ctr[2], ALPHA[2], lc, ctr[3], ALPHA[3], ld)
@@ -89,8 +101,9 @@ def run_case(kx, T, precision):
         err = np.abs(got - ref).max()
         K0 = oracle.exchange_direct(s, P)
         err_all = np.abs(K - K0).max()
-        if precision == "fp64":
+        if precision in ("fp64", "dw"):
             assert err <= TOL64 and err_all <= TOL64, (cls, T, err, err_all)
+            worst = max(worst, err)
         else:
             s2 = oracle.schwarz_sq(s)
             beta = np.sqrt(s2[0, 1]) * np.linalg.norm(Pbd) * np.sqrt(s2[2, 3])
@@ -109,3 +122,9 @@ def test_every_class_at_boys_argument_fp64(kx, T):
 def test_every_class_at_boys_argument_fp32(kx, T):
     worst = run_case(kx, T, "fp32")
     print(f"T = {T:g}: largest FP32 error {worst:.2f} eps32 beta")
+
+
+@pytest.mark.parametrize("T", T_VALUES)
+def test_every_class_at_boys_argument_double_word(kx, T):
+    worst = run_case(kx, T, "dw")
+    print(f"T = {T:g}: largest double-word error {worst:.2e}")

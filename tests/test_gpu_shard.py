@@ -1,9 +1,13 @@
 """K row-block shards on one GPU: the shards of a build, run one after the
 other, must reproduce the whole build.  The worklists of the shards are
-disjoint and their union is the build's worklist (bit-exact); the sum of
-their K equals the whole K (FP64 atomics in another order: 1e-12); their
-survivor counts add up exactly; a captured shard replays the eager shard.
-The shards come from kx_row_work and kx_shard_bounds (balanced ERI work)."""
+disjoint and their union is the build's worklist (bit-exact); their
+survivor counts add up exactly; the sum of their K equals the whole K and a
+captured shard replays the eager shard.  In FP64 the only difference is the
+order of the FP64 atomic adds (1e-12 relative).  In mixed precision the
+FP32 partial sums of a warp depend on which records share the warp, which
+differs between a shard and the whole build, so there the bar is the
+contract's mixed-precision 1e-8.  The shards come from kx_row_work and
+kx_shard_bounds (balanced ERI work)."""
 import numpy as np
 import pytest
 
@@ -23,6 +27,10 @@ def kx():
     import paper_1401_6961_gb300 as kx
     kx.load()
     return kx
+
+
+def _tol(opts, K):
+    return 1e-8 if opts.get("precision", 0) == 1 else 1e-12 * max(1.0, K.abs().max().item())
 
 
 def _sorted(w):
@@ -67,7 +75,7 @@ def test_shards_reproduce_the_build(kx, case, symmetric):
         torch.cuda.synchronize()
         assert nq == st0.n_shell_quartets
         assert np.array_equal(_sorted(np.concatenate(lists)), w0)
-        assert (Ks - K0).abs().max().item() <= 1e-12 * max(1.0, K0.abs().max().item())
+        assert (Ks - K0).abs().max().item() <= _tol(opts, K0)
     ex.close()
 
 
@@ -85,7 +93,15 @@ def test_captured_shard_replays_the_eager_shard(kx):
     ex.plan(Pd, K, **so)
     ex.replay()
     torch.cuda.synchronize()
-    assert (K - Ke).abs().max().item() <= 1e-12 * max(1.0, Ke.abs().max().item())
+    assert (K - Ke).abs().max().item() <= _tol(opts, Ke)
+    # and in FP64 to rounding order
+    o64 = dict(opts, precision=0)
+    so = shard.shard_opts(b, 1, **o64)
+    Ke = ex(Pd, **so).clone()
+    ex.plan(Pd, K, **so)
+    ex.replay()
+    torch.cuda.synchronize()
+    assert (K - Ke).abs().max().item() <= _tol(o64, Ke)
     ex.close()
 
 
