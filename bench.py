@@ -36,7 +36,8 @@ UNIT = "K-builds/s"
 WORKLOADS = ("water64", "water16", "batch256")
 BATCH_TAU = 1e-8
 TAU = 1e-10
-SPLIT = 5e-4          # measured max|dK| vs FP64: 3.0e-9 on (H2O)64, 1.7e-9 on the batch
+SPLIT = 5e-4          # fixed split of the studies and the batch (measured max|dK| vs FP64: 3.0e-9 on (H2O)64)
+SPLIT_BUDGET = 8e-9   # FP32 share of the 1e-8 bar: the benchmark build's split comes from kx_split_plan
 BENCH_LEAF = 16       # leaf size of the benchmark builds (fastest of 10, 16, 20, 32 on (H2O)64)
 L2_FLUSH_BYTES = 256 << 20
 # headline precision: FP32 below the split, FP64 above ("mixed") or double-word FP32 above ("mixed_dw")
@@ -144,9 +145,30 @@ def max_over_ranks(x: float, ws: int, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, ws: int, device) -> float:
+    """The sum of every rank's x."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_rate(units_per_rank: float, ws: int, seconds_max: float) -> float:
     """Whole-job throughput: the units of every rank over the slowest rank's time."""
     return ws * units_per_rank / seconds_max
+
+
+PREC_NAME = ("fp64", "fp32", "dw")
+
+
+def measured_alu_peaks(kx, device: int) -> dict:
+    """TFLOP/s of the FP64 and FP32 FMA pipes and of double-word FP32
+    multiply-adds, measured by the library's probes on this GPU."""
+    return {"fp64": kx.kx_peak_probe(device, kx.KX_FP64) / 1e3, "fp32": kx.kx_peak_probe(device, kx.KX_MIXED) / 1e3,
+            "dw": kx.kx_peak_probe(device, kx.KX_PROBE_DW) / 1e3}
 
 
 def measured_peak(name: str):
@@ -161,20 +183,78 @@ def measured_peak(name: str):
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(sys_, P, n_rows: int, seed: int = 1, leaf_max: int = 10):
-    """Exact screened K rows of n_rows sampled shells; returns (seconds,
-    extrapolated K-builds/s, threads, description)."""
-    import numpy as np
+ORACLE_ROW_SEED = 16   # the fixed seeded set of K-row shells the oracle samples
 
+
+def oracle_row_set(sys_, n: int = 16, seed: int = ORACLE_ROW_SEED):
+    """A fixed set of n K-row shells stratified by angular momentum: about
+    n * (share of l among the shells) of each l, at least one of each l
+    present, drawn with a fixed seed."""
+    import numpy as np
+    L = np.asarray(sys_.shell_l)
+    rng = np.random.default_rng(seed)
+    groups = []
+    for l in sorted(set(L.tolist())):
+        idx = np.nonzero(L == l)[0]
+        k = max(1, int(round(n * len(idx) / len(L))))
+        groups.append([int(x) for x in rng.choice(idx, size=min(k, len(idx)), replace=False)])
+    # interleave the types (highest l first) so that any prefix mixes them
+    rows = []
+    for i in range(max(len(g) for g in groups)):
+        rows += [g[i] for g in reversed(groups) if i < len(g)]
+    return rows
+
+
+def oracle_row_times(sys_, P, rows, leaf_max: int = 10, tau: float = None):
+    """Seconds of the oracle's exact screened K rows of each shell in rows."""
     import oracle
     oracle.build()
-    rows = [int(x) for x in np.random.default_rng(seed).choice(sys_.n_shell, size=n_rows, replace=False)]
-    t0 = time.perf_counter()
-    oracle.exchange_screened(sys_, P, TAU, leaf_max=leaf_max, rows=rows)
-    dt = time.perf_counter() - t0
-    full = dt * sys_.n_shell / n_rows
-    desc = (f"oracle (FP64 C, OpenMP) screened exchange of {n_rows} sampled K-row shells of "
-            f"{sys_.n_shell} ({dt:.1f} s), extrapolated linearly to the full build")
+    out = []
+    for r in rows:
+        t0 = time.perf_counter()
+        oracle.exchange_screened(sys_, P, TAU if tau is None else tau, leaf_max=leaf_max, rows=[r])
+        out.append((r, int(sys_.shell_l[r]), time.perf_counter() - t0))
+    return out
+
+
+def extrapolate_rows(sys_, times) -> float:
+    """Seconds of a full build from row timings: for each angular momentum,
+    its shell count times the mean time of its sampled rows (the mean of all
+    sampled rows for a type that was not sampled)."""
+    import numpy as np
+    L = np.asarray(sys_.shell_l)
+    allmean = float(np.mean([t for _, _, t in times]))
+    total = 0.0
+    for l in sorted(set(L.tolist())):
+        ts = [t for _, ll, t in times if ll == l]
+        total += int((L == l).sum()) * (float(np.mean(ts)) if ts else allmean)
+    return total
+
+
+def host_cpu() -> str:
+    """CPU model and core count of this host (lscpu)."""
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        model = next((ln.split(":", 1)[1].strip() for ln in txt.splitlines() if ln.startswith("Model name")), "?")
+        arch = next((ln.split(":", 1)[1].strip() for ln in txt.splitlines() if ln.startswith("Architecture")), "?")
+    except (OSError, subprocess.SubprocessError):
+        model, arch = "?", "?"
+    return f"{os.cpu_count()} x {model} ({arch})"
+
+
+def oracle_sample(sys_, P, n_rows: int, seed: int = 1, leaf_max: int = 10):
+    """Exact screened K rows of the first n_rows shells of the fixed
+    stratified row set, extrapolated per angular momentum to the full build;
+    returns (seconds, K-builds/s, threads, description)."""
+    import oracle
+    rows = oracle_row_set(sys_)[:n_rows]
+    times = oracle_row_times(sys_, P, rows, leaf_max)
+    dt = sum(t for _, _, t in times)
+    full = extrapolate_rows(sys_, times)
+    desc = (f"oracle (FP64 C, OpenMP) screened exchange of {len(rows)} K-row shells (l = "
+            f"{','.join(str(l) for _, l, _ in times)}) of {sys_.n_shell}, from a fixed seeded set stratified by "
+            f"angular momentum ({dt:.1f} s), extrapolated per angular momentum to the full build; host "
+            f"{host_cpu()}")
     return dt, 1.0 / full, oracle.num_threads(), desc
 
 
@@ -227,17 +307,22 @@ def run_reference(args):
         print(json.dumps(line), flush=True)
         return
     sys_, P = wl.workload(args.workload)
-    # warm-up steps and timed steps, each a bounded sample of the workload
-    times = []
-    rates = []
-    threads = 1
-    desc = ""
+    # warm-up steps and timed steps, each a bounded sample of the workload:
+    # step i times the next ref_rows shells of the fixed stratified row set
+    import oracle
+    rowset = oracle_row_set(sys_)
+    timed = []
     for i in range(args.warmup + args.steps):
-        dt, rate, threads, desc = oracle_sample(sys_, P, args.ref_rows, seed=100 + i, leaf_max=args.leaf_max)
+        rows = [rowset[(i * args.ref_rows + k) % len(rowset)] for k in range(args.ref_rows)]
+        t = oracle_row_times(sys_, P, rows, args.leaf_max)
         if i >= args.warmup:
-            times.append(dt)
-            rates.append(rate)
-    v = statistics.mean(rates)
+            timed += t
+    v = 1.0 / extrapolate_rows(sys_, timed)
+    threads = oracle.num_threads()
+    desc = (f"oracle (FP64 C, OpenMP) screened exchange of K-row shells from a fixed set of {len(rowset)} "
+            f"stratified by angular momentum, {args.ref_rows} per step ({len(timed)} timed rows, "
+            f"{sum(t for _, _, t in timed):.1f} s), extrapolated per angular momentum to the full build; host "
+            f"{host_cpu()}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -247,16 +332,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(sys_, precision, name, symmetric=True, leaf_max=10):
+def workload_config(sys_, precision, name, symmetric=True, leaf_max=10, split=SPLIT, parallelism="replicas"):
     nw = sys_.n_atom // 3
     return {"workload": f"(H2O){nw} water cluster at 1 g/cm^3, even-tempered medium basis "
                         f"({sys_.n_fn} functions, {sys_.n_shell} shells), tau=1e-10",
             "name": name,
             "n_fn": sys_.n_fn, "n_shell": sys_.n_shell, "tau": TAU, "leaf_max": leaf_max,
-            "precision": precision, "split_threshold": SPLIT if precision.startswith("mixed") else None,
+            "precision": precision, "split_threshold": split if precision.startswith("mixed") else None,
             "shell_screen": True, "symmetric": bool(symmetric),
             "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB buffer written)",
-            "parallelism": "replicas"}
+            "parallelism": parallelism}
 
 
 def batch_config(systems, precision, symmetric=True, leaf_max=10):
@@ -335,12 +420,11 @@ def run_batch(args):
     prof = kx.kx_get_profile(bx.ctx)
     ste = bx.stats
     s_dom = int(np.argmax(prof["ms"]))
-    prec_dom = "fp64" if s_dom < 81 else "fp32"
+    prec_dom = PREC_NAME[s_dom // 81]
     cls = s_dom % 81
     la, lb, lc, ld = cls // 27, (cls // 9) % 3, (cls // 3) % 3, cls % 3
-    peak64 = kx.kx_peak_probe(local, kx.KX_FP64) / 1e3
-    peak32 = kx.kx_peak_probe(local, kx.KX_MIXED) / 1e3
-    peak = peak64 if prec_dom == "fp64" else peak32
+    peaks = measured_alu_peaks(kx, local)
+    peak = peaks[prec_dom]
     achieved = prof["flops"][s_dom] / (prof["ms"][s_dom] * 1e-3) / 1e12
 
     fp64 = None
@@ -394,7 +478,7 @@ def run_batch(args):
                          "kernel": kernel_name(kx, bx.ctx, s_dom),
                          "measured": "CUDA events around each launch of that kernel in an eager profiled build "
                                      "of the same batch (a graph replay cannot be split by events)",
-                         "peak_source": f"measured FMA probe ({prec_dom} pipe), kx_peak_probe"},
+                         "peak_source": f"measured probe ({prec_dom}), kx_peak_probe"},
             "fp64_plain": fp64,
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "max_abs_dK_vs_fp64": diff,
@@ -434,8 +518,32 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sym = 0 if args.no_symmetric else 1
     prec = PRECISION[args.precision](kx)
-    mixed = dict(tau=TAU, precision=prec, split_threshold=SPLIT, profile=1, symmetric=sym)
+    # the split: from the FP32 error budget (kx_split_plan, untimed set-up), or fixed
+    if args.split_budget > 0:
+        sp = ex.split_plan(Pd, args.split_budget, tau=TAU, symmetric=sym)
+        split = sp.split_used
+        split_info = {"budget": args.split_budget, "split": split, "fp32_err_estimate_5sigma": sp.fp32_err_estimate,
+                      "fp32_err_bound": sp.fp32_err_bound, "how": "kx_split_plan: per-class FP32 error constants, "
+                      "sampled K shell blocks, largest tau*2^k whose 5-sigma estimate fits the budget"}
+    else:
+        split = SPLIT
+        split_info = {"split": split, "how": "fixed"}
+    mixed = dict(tau=TAU, precision=prec, split_threshold=split, profile=1, symmetric=sym)
     plain = dict(tau=TAU, precision=kx.KX_FP64, profile=1, symmetric=sym)
+    # several ranks: each builds the K rows of its balanced row-block shard
+    # (kx_row_work / kx_shard_bounds; every rank computes the same plan) and
+    # one sum over the ranks assembles K inside the timed step
+    sharded = ws > 1 and not args.replicas
+    if sharded:
+        from paper_1401_6961_gb300 import shard
+        bounds = shard.plan(ex, Pd, ws, tau=TAU, precision=prec, split_threshold=split, symmetric=sym)
+        rows = dict(row_leaf_lo=int(bounds[rank]), row_leaf_hi=int(bounds[rank + 1]))
+        mixed.update(rows)
+        plain.update(rows)
+
+    def assemble(K):
+        if sharded:
+            shard.assemble(K)
 
 
     def timed_steps(opts, steps):
@@ -480,6 +588,7 @@ def run_ours(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             ex.replay()
+            assemble(Kd)
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize(dev)
@@ -487,8 +596,11 @@ def run_ours(args):
     st = ex.stats
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
     ms_step = ms / args.steps
-    value = job_rate(1, ws, ms_step * 1e-3)
+    # replicas: every rank built a whole K; shards: the ranks built one K together
+    value = job_rate(1, 1 if sharded else ws, ms_step * 1e-3)
     quartets = st.n_shell_quartets
+    # every rank's quartets: a shard's own, a replica's whole build
+    quartets_all = sum_over_ranks(float(quartets), ws, dev)
     launches = int(st.n_launches) * args.steps
     Kmix = Kd.clone()
 
@@ -502,15 +614,15 @@ def run_ours(args):
 
     # roofline of the dominant ERI class kernel over the timed steps
     s_dom = int(np.argmax(prof["ms"]))
-    prec_dom = "fp64" if s_dom < 81 else "fp32"
+    prec_dom = PREC_NAME[s_dom // 81]
     cls = s_dom % 81
     la, lb, lc, ld = cls // 27, (cls // 9) % 3, (cls // 3) % 3, cls % 3
     dom_ms = prof["ms"][s_dom]
     dom_launch = max(prof["launches"][s_dom], 1)
     achieved = prof["flops"][s_dom] / (dom_ms * 1e-3) / 1e12
-    peak64 = kx.kx_peak_probe(local, kx.KX_FP64) / 1e3
-    peak32 = kx.kx_peak_probe(local, kx.KX_MIXED) / 1e3
-    peak = peak64 if prec_dom == "fp64" else peak32
+    peaks = measured_alu_peaks(kx, local)
+    peak64, peak32, peakdw = peaks["fp64"], peaks["fp32"], peaks["dw"]
+    peak = peaks[prec_dom]
     eri_ms = float(prof["ms"].sum())
     # every class stream of the eager builds, on stderr
     streams = []
@@ -518,7 +630,7 @@ def run_ours(args):
         if prof["ms"][s_] > 0:
             c_ = s_ % 81
             streams.append({"stream": s_, "class": "({}{}|{}{})".format(*("spd"[x] for x in (
-                c_ // 27, (c_ // 9) % 3, (c_ // 3) % 3, c_ % 3))), "precision": "fp64" if s_ < 81 else "fp32",
+                c_ // 27, (c_ // 9) % 3, (c_ // 3) % 3, c_ % 3))), "precision": PREC_NAME[s_ // 81],
                 "kernel": kernel_name(kx, ex.ctx, s_), "ms": float(prof["ms"][s_]), "quartets": int(prof["n"][s_]),
                 "tflops": float(prof["flops"][s_] / (prof["ms"][s_] * 1e-3) / 1e12)})
     print(json.dumps({"eri_streams": streams}), file=sys.stderr, flush=True)
@@ -531,12 +643,18 @@ def run_ours(args):
         c_ = s_ % 81
         top.append({"class": "({}{}|{}{})".format(*("spd"[x] for x in (c_ // 27, (c_ // 9) % 3, (c_ // 3) % 3,
                                                                        c_ % 3))),
-                    "precision": "fp64" if s_ < 81 else "fp32", "kernel": kernel_name(kx, ex.ctx, s_),
+                    "precision": PREC_NAME[s_ // 81], "kernel": kernel_name(kx, ex.ctx, s_),
                     "ms": float(prof["ms"][s_]) / max(1, args.eager_steps),
                     "quartets": int(prof["n"][s_]) // max(1, args.eager_steps),
                     "tflops": float(prof["flops"][s_] / (prof["ms"][s_] * 1e-3) / 1e12)})
     eri_flops64 = float(prof["flops"][:81].sum())
-    eri_flops32 = float(prof["flops"][81:].sum())
+    eri_flops32 = float(prof["flops"][81:162].sum())
+    eri_flopsdw = float(prof["flops"][162:].sum())
+    # step-level ALU fraction: the time the step's algorithmic FLOPs need at
+    # the measured peak of the pipe each runs on, over the measured step
+    steps_e = max(1, args.eager_steps)
+    floor_ms = 1e3 * (eri_flops64 / (peak64 * 1e12) + eri_flops32 / (peak32 * 1e12)
+                      + eri_flopsdw / (peakdw * 1e12)) / steps_e
 
     # plain FP64 build of the same system (the speed-up denominator)
     # plain FP64 build of the same system, captured and replayed the same way
@@ -549,46 +667,74 @@ def run_ours(args):
         e0.record(stream)
         for _ in range(args.fp64_steps):
             ex.replay()
+            assemble(Kd)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = max_over_ranks(e0.elapsed_time(e1), ws, dev) / args.fp64_steps
         s64 = ex.stats
         diff = float((Kmix - Kd).abs().max().item())
-        fp64 = {"value": ws * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
-                "warmup": 0, "launch": "captured graph, replayed",
+        K64 = Kd.clone()
+        fp64 = {"value": (1 if sharded else ws) * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                "steps": args.fp64_steps, "warmup": 0, "launch": "captured graph, replayed",
                 "quartets_per_s": ws * s64.n_shell_quartets / (ms64 * 1e-3),
                 "build_tflops_fp64": s64.flops_fp64 / (ms64 * 1e-3) / 1e12,
                 "build_frac_of_fp64_peak": s64.flops_fp64 / (ms64 * 1e-3) / 1e12 / peak64}
     else:
         diff = None
 
+    # the contract's literal split precision (FP64 above the split), captured
+    # and replayed the same way, when the headline uses double words there
+    lit = None
+    if args.precision != "mixed" and args.fp64_steps > 0:
+        ex.plan(Pd, Kd, headroom=0.25, **dict(nomix, precision=kx.KX_MIXED))
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            ex.replay()
+            assemble(Kd)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        msl = max_over_ranks(e0.elapsed_time(e1), ws, dev) / args.fp64_steps
+        lit = {"value": (1 if sharded else ws) * 1e3 / msl, "unit": UNIT, "ms_per_step": msl, "steps": args.fp64_steps,
+               "precision": "fp32 below the split, fp64 above", "shell_quartets_fp64": ex.stats.n_shell_quartets_fp64,
+               "launch": "captured graph, replayed",
+               "max_abs_dK_vs_fp64": float((Kd - K64).abs().max().item()) if fp64 else None}
+
     # end to end through the host-buffer entry point (pinned host P and K)
     e2e = None
     if args.e2e_steps > 0:
         Ph = torch.from_numpy(P).pin_memory().numpy()
         Kh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
-        ex.host(Ph, tau=TAU, precision=prec, split_threshold=SPLIT, symmetric=sym)
+        ex.host(Ph, tau=TAU, precision=prec, split_threshold=split, symmetric=sym)
         barrier(ws)
         t0 = time.perf_counter()
+        ho = {k: v for k, v in nomix.items()}
         for _ in range(args.e2e_steps):
-            kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(tau=TAU, precision=prec,
-                                                               split_threshold=SPLIT, symmetric=sym), Kh)
+            kx.kx_exchange_host(ex.ctx, Ph, kx.kx_default_opts(**ho), Kh)
         dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
-        e2e = {"value": ws * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
+        e2e = {"value": (1 if sharded else ws) * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
                "d2h_bytes_per_step": 8 * n * n}
+        if sharded:
+            e2e["note"] = "each rank copies P in and its shard's K out; the sum over ranks is not in this figure"
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        dt, rate, thr, desc = oracle_sample(sys_, P, args.ref_rows, leaf_max=args.leaf_max)
+        # the first three shells of the fixed row set: one of each angular momentum
+        dt, rate, thr, desc = oracle_sample(sys_, P, 3, leaf_max=args.leaf_max)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": workload_config(sys_, args.precision, args.workload, sym, args.leaf_max),
-            "quartets_per_s": ws * quartets / (ms_step * 1e-3),
+            "config": workload_config(sys_, args.precision, args.workload, sym, args.leaf_max, split,
+                                      "row-block shards, one all-reduce of K per step" if sharded else "replicas"),
+            "split": split_info,
+            "quartets_per_s": quartets_all / (ms_step * 1e-3),
             "shell_quartets": quartets, "leaf_quartets": st.n_leaf_quartets,
             "shell_quartets_fp64": st.n_shell_quartets_fp64, "shell_quartets_dw": st.n_shell_quartets_dw,
             "launch": "one captured CUDA graph per build (kx_graph_plan / kx_graph_launch), autotuned "
@@ -605,16 +751,23 @@ def run_ours(args):
                          "ms_per_launch": dom_ms / dom_launch,
                          "measured": "CUDA events on the launching stream around each launch of that kernel, "
                                      "in the eager builds of the same system that follow the timed replays",
-                         "peak_source": f"measured FMA probe ({prec_dom} pipe), kx_peak_probe"},
+                         "peak_source": f"measured probe ({prec_dom}), kx_peak_probe"},
             "eri_classes_top": top,
             "eri_stage": {"ms_per_step": eri_ms / max(1, args.eager_steps),
-                          "tflops": (eri_flops64 + eri_flops32) / (eri_ms * 1e-3) / 1e12,
-                          "flops_fp64_per_step": eri_flops64 / max(1, args.eager_steps),
-                          "flops_fp32_per_step": eri_flops32 / max(1, args.eager_steps),
-                          "peak_fp64_tflops": peak64, "peak_fp32_tflops": peak32},
+                          "tflops": (eri_flops64 + eri_flops32 + eri_flopsdw) / (eri_ms * 1e-3) / 1e12,
+                          "flops_fp64_per_step": eri_flops64 / steps_e,
+                          "flops_fp32_per_step": eri_flops32 / steps_e,
+                          "flops_dw_per_step": eri_flopsdw / steps_e,
+                          "peak_fp64_tflops": peak64, "peak_fp32_tflops": peak32, "peak_dw_tflops": peakdw},
+            "step_roofline": {"bound": "alu", "floor_ms": floor_ms, "ms_per_step": ms_step,
+                              "frac": floor_ms / ms_step, "eri_frac": floor_ms / (eri_ms / steps_e),
+                              "how": "algorithmic FLOPs of each precision at its measured peak (kx_peak_probe: "
+                                     "FP64 and FP32 FMA pipes, double-word FMA chains), summed, over the "
+                                     "replayed step and over the ERI stage of the eager step"},
             "fp64_plain": fp64,
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "max_abs_dK_vs_fp64": diff,
+            "mixed_fp64_above_split": lit,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -823,13 +976,17 @@ def main():
     ap.add_argument("--workload", choices=WORKLOADS, default="water64",
                     help="water64 is the benchmark; water16 is a small case for profiling; batch256 is the "
                          "batched workload (256 clusters per step, captured graph)")
-    ap.add_argument("--precision", choices=sorted(PRECISION), default="mixed",
+    ap.add_argument("--precision", choices=sorted(PRECISION), default="mixed_dw",
                     help="headline build: FP32 below the split and FP64 (mixed) or double-word FP32 (mixed_dw) above")
+    ap.add_argument("--split-budget", type=float, default=SPLIT_BUDGET,
+                    help="FP32 error budget of the split planner; 0 = the fixed split")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--eager-steps", type=int, default=1, help="profiled eager builds after the timed replays")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-rows", type=int, default=2, help="K-row shells per oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun, every rank builds the whole K instead of its row-block shard")
     ap.add_argument("--no-symmetric", action="store_true",
                     help="build every K block instead of the A <= C half and its mirror")
     ap.add_argument("--leaf-max", type=int, default=BENCH_LEAF,

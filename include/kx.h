@@ -334,10 +334,12 @@ int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32
 /* Throughput probe on `device`, timed with CUDA events (best of five after
  * a warm-up launch).  precision KX_FP64 or KX_MIXED (= FP32): independent
  * fused multiply-add chains on the plain FMA pipe; KX_PROBE_FP64_MMA: FP64
- * tensor-core (DMMA, mma.sync m8n8k4) chains.  *gflops = measured GFLOP/s
- * (2 per multiply-add).  Not part of the exchange build; used to state
+ * tensor-core (DMMA, mma.sync m8n8k4) chains; KX_PROBE_DW: double-word FP32
+ * multiply-add chains (the arithmetic of KX_MIXED_DW).  *gflops = measured
+ * GFLOP/s (2 per multiply-add).  Not part of the exchange build; used to state
  * roofline fractions and to decide where tensor cores would pay. */
 #define KX_PROBE_FP64_MMA 2
+#define KX_PROBE_DW 3
 int kx_peak_probe(int device, int precision, double* gflops);
 
 /* ------------------------------------------------------------------------
@@ -371,9 +373,9 @@ int kx_traverse(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, int64
 int kx_leaf_features(kx_ctx* c, float* feat, int64_t cap, int64_t* n);
 
 /* Drops kept leaf quartet i = (A,B,C,D) when its bound is at most 10 tau
- * and pred[i] + log10(m_AC)/2 < log10_budget, m_AC being the number of kept
+ * and pred[i] + log10(m_AC) < log10_budget, m_AC being the number of kept
  * quartets of bound <= 10 tau that share its K block (A,C): the predicted
- * root-sum-square of what any K block loses stays below the budget.  pred: DEVICE
+ * sum of what any K block loses stays below the budget.  pred: DEVICE
  * array in kept order (log10 contributions, any safety margin added by the
  * caller).  Keeps the order of the rest; *n_kept = what remains. */
 int kx_cull_kept(kx_ctx* c, const float* pred, double tau, double log10_budget, int64_t* n_kept);
@@ -462,6 +464,15 @@ int kx_mlp_adam(float* params, const float* grad, float* m, float* v, float lr, 
  * others are expanded and *n_next counts their children). */
 int kx_traverse_level_noalloc(kx_ctx* c, int32_t level, const uint16_t* front, int64_t n,
                               double tau, uint16_t* next, int64_t cap, int64_t* n_next);
+
+/* Algorithmic FLOPs of one shell quartet of class cls = ((la*3 + lb)*3 +
+ * lc)*3 + ld, as the build counts them (*total), and the part of it that
+ * does not involve P (*integral: P-Q, the prefactor, the Boys function and
+ * the Hermite recursion of R; the rest is the contraction with P through
+ * the Hermite sets).  An integral block shared by several symmetric images
+ * (the index swaps of Eq. 9) could save the integral part of all but one,
+ * never the contraction.  Host only; KX_EINVAL for a bad class or pointer. */
+int kx_class_flops(int32_t cls, double* total, double* integral);
 
 /* Last error message of the context (never NULL). */
 const char* kx_last_error(const kx_ctx* c);

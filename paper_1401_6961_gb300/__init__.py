@@ -14,6 +14,6 @@ from ._binding import (  # noqa: F401
     kx_traverse, kx_leaf_features, kx_cull_kept, kx_evaluate_kept, kx_exchange_leaves, kx_block_norms,
     kx_mlp_infer_bf16, kx_mlp_loss_grad, kx_mlp_adam, KX_NFEAT, KX_MLP_HIDDEN, KX_MLP_NPARAM, kx_last_error, kx_n_functions, kx_opts,
     kx_stats, library_path, load, kx_create_batch, kx_exchange_batch, kx_exchange_batch_host, kx_packed_size,
-    kx_autotune, kx_get_launch_shapes, kx_set_launch_shape, kx_graph_plan, kx_graph_launch, KX_PROBE_FP64_MMA,
-    kx_row_work, kx_shard_bounds, kx_split_plan,
+    kx_autotune, kx_get_launch_shapes, kx_set_launch_shape, kx_graph_plan, kx_graph_launch, KX_PROBE_FP64_MMA, KX_PROBE_DW,
+    kx_row_work, kx_shard_bounds, kx_split_plan, kx_class_flops,
 )

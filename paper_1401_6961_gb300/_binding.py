@@ -28,12 +28,13 @@ EXPORTS = ["kx_default_opts", "kx_create", "kx_build_schwarz", "kx_build_tree", 
            "kx_get_norms", "kx_get_profile", "kx_peak_probe", "kx_traverse_level_noalloc",
            "kx_traverse", "kx_leaf_features", "kx_cull_kept", "kx_evaluate_kept", "kx_exchange_leaves",
            "kx_block_norms", "kx_mlp_infer_bf16", "kx_mlp_loss_grad", "kx_mlp_adam",
-           "kx_row_work", "kx_shard_bounds", "kx_split_plan", "kx_last_error", "kx_destroy"]
+           "kx_row_work", "kx_shard_bounds", "kx_split_plan", "kx_class_flops", "kx_last_error", "kx_destroy"]
 KX_NFEAT = 10
 KX_MLP_HIDDEN = 64
 KX_MLP_NPARAM = 9109
 KX_NOALLOC_MAX_TASKS = 1 << 18
 KX_PROBE_FP64_MMA = 2
+KX_PROBE_DW = 3
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -127,6 +128,7 @@ def load() -> ctypes.CDLL:
     L.kx_split_plan.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), ctypes.c_double,
                                 ctypes.POINTER(kx_stats)]
     L.kx_shard_bounds.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int32, _i32p]
+    L.kx_class_flops.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.kx_traverse_level_noalloc.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_double, vp,
                                             ctypes.c_int64, _i64p]
     L.kx_traverse.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(kx_opts), _i64p]
@@ -353,7 +355,8 @@ def kx_get_profile(ctx) -> dict:
 
 def kx_peak_probe(device: int = 0, precision: int = KX_FP64) -> float:
     """Measured throughput in GFLOP/s: the FMA pipe (FP64 or, with KX_MIXED,
-    FP32) or, with KX_PROBE_FP64_MMA, the FP64 tensor cores (DMMA)."""
+    FP32), with KX_PROBE_FP64_MMA the FP64 tensor cores (DMMA), with
+    KX_PROBE_DW double-word FP32 multiply-adds."""
     g = ctypes.c_double()
     r = load().kx_peak_probe(int(device), int(precision), ctypes.byref(g))
     if r != KX_OK:
@@ -377,6 +380,16 @@ def kx_split_plan(ctx, P_ptr: int, ldp: int, opts: kx_opts, budget: float) -> kx
     _check(ctx, load().kx_split_plan(ctx, ctypes.c_void_p(P_ptr), int(ldp), ctypes.byref(opts), float(budget),
                                      ctypes.byref(st)))
     return st
+
+
+def kx_class_flops(cls: int):
+    """(total, integral) algorithmic FLOPs of one quartet of class cls
+    (host computation)."""
+    t, i = ctypes.c_double(), ctypes.c_double()
+    r = load().kx_class_flops(int(cls), ctypes.byref(t), ctypes.byref(i))
+    if r != KX_OK:
+        raise KxError(r, "kx_class_flops failed")
+    return float(t.value), float(i.value)
 
 
 def _n_leaves(ctx):

@@ -98,8 +98,12 @@ def tables(res: dict) -> str:
     cmax = [1.5 * res[c]["max"] if c in res else 10.0 for c in range(81)]
     crms = [res[c]["rms"] if c in res else 2.0 for c in range(81)]
 
+    def lit(x):
+        t = f"{x:.3g}"
+        return (t if ("." in t or "e" in t) else t + ".0") + "f"
+
     def fmt(v):
-        return "\n".join("    " + ", ".join(f"{x:.3g}f" for x in v[i:i + 9]) + "," for i in range(0, 81, 9))
+        return "\n".join("    " + ", ".join(lit(x) for x in v[i:i + 9]) + "," for i in range(0, 81, 9))
     return "CMAX\n" + fmt(cmax) + "\nCRMS\n" + fmt(crms)
 
 

@@ -401,6 +401,13 @@ int kx_row_work(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, doubl
     return KX_OK;
 }
 
+int kx_class_flops(int32_t cls, double* total, double* integral) {
+    if (cls < 0 || cls >= NCLASS || !total || !integral) return KX_EINVAL;
+    *total = class_flops(cls);
+    *integral = integral_flops(class_l(cls));
+    return KX_OK;
+}
+
 int kx_shard_bounds(const double* work, int32_t n_leaf, int32_t n_shards, int32_t* bounds) {
     if (!work || !bounds || n_leaf < 1 || n_shards < 1 || n_shards > n_leaf) return KX_EINVAL;
     double total = 0.0;
@@ -673,7 +680,8 @@ int kx_get_profile(const kx_ctx* c, double* ms, int64_t* n, double* flops, int32
 }
 
 int kx_peak_probe(int device, int precision, double* gflops) {
-    if (!gflops || (precision != KX_FP64 && precision != KX_MIXED && precision != KX_PROBE_FP64_MMA))
+    if (!gflops || (precision != KX_FP64 && precision != KX_MIXED && precision != KX_PROBE_FP64_MMA &&
+                    precision != KX_PROBE_DW))
         return KX_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

@@ -1284,17 +1284,7 @@ template <int LA, int LB, int LC, int LD>
 double eri_flops() {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
-    double f = 0;
-    f += 20;                                  // P-Q, rho, T, prefactor
-    f += 6 + (L + 1) * (2 * 6 + 1) + L;       // Boys (Taylor) and scaling
-    for (int n = L - 1; n >= 0; --n)          // Hermite recursion
-        for (int j = L - n; j >= 1; --j)
-            for (int t = j; t >= 0; --t)
-                for (int u = j - t; u >= 0; --u) {
-                    int v = j - t - u;
-                    int k = t > 0 ? t : (u > 0 ? u : v);
-                    f += (k > 1) ? 3 : 1;
-                }
+    double f = integral_flops(L);             // set-up, Boys, Hermite recursion
     auto nreach = [](int Lh, int x, int y, int z, int l2) {
         int n = 0;
         for (int t = 0; t <= Lh; ++t)

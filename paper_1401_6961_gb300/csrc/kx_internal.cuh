@@ -498,6 +498,23 @@ int eri_prepare(kx_ctx* c, int s, int variant, const EriKern& k);
 
 // algorithmic FLOPs of one shell quartet of a class (the counter of the ERI kernels)
 double class_flops(int cls);
+// the part of it that does not depend on P: P-Q, rho, T and the prefactor,
+// the Boys function (Taylor) with its scaling, and the Hermite recursion of
+// R_tuv for t+u+v <= L (every class of total angular momentum L alike); the
+// rest of class_flops is the contraction with P through the Hermite sets
+inline double integral_flops(int L) {
+    double f = 20;                            // P-Q, rho, T, prefactor
+    f += 6 + (L + 1) * (2 * 6 + 1) + L;       // Boys (Taylor) and scaling
+    for (int n = L - 1; n >= 0; --n)          // Hermite recursion
+        for (int j = L - n; j >= 1; --j)
+            for (int t = j; t >= 0; --t)
+                for (int u = j - t; u >= 0; --u) {
+                    const int v = j - t - u;
+                    const int k = t > 0 ? t : (u > 0 ? u : v);
+                    f += (k > 1) ? 3 : 1;
+                }
+    return f;
+}
 int peak_probe(int device, int precision, double* gflops);   // kx_setup.cu
 
 }  // namespace kx

@@ -128,11 +128,11 @@ __global__ void k_cull_count(const Task* __restrict__ w, int64_t n, int nl, cons
 }
 
 // Culls quartet i iff its bound is at most 10 tau and its predicted
-// contribution times the square root of the number m of cullable quartets
-// of its K block is below the budget: the predicted root-sum-square of what
-// any K block loses then stays below the budget (the dropped contributions
-// carry varying signs, so their sum grows like sqrt(m) times a typical one).
-// A quartet whose exact bound exceeds 10 tau is never culled.
+// contribution times the number m of cullable quartets of its K block is
+// below the budget: the predicted sum of what any K block loses then stays
+// below the budget whatever the signs of the dropped contributions.  (A
+// root-sum-square rule, sqrt(m) in place of m, let (H2O)_256 lose 1.5e-8 at
+// tau = 1e-8.)  A quartet whose exact bound exceeds 10 tau is never culled.
 __global__ void k_cull_flags(const Task* __restrict__ w, int64_t n, int nl, const double* __restrict__ S,
                              const double* __restrict__ Pn, const float* __restrict__ pred, double ten_tau,
                              float log10_budget, const int* __restrict__ cnt, int64_t* __restrict__ keep) {
@@ -141,7 +141,7 @@ __global__ void k_cull_flags(const Task* __restrict__ w, int64_t n, int nl, cons
         bool cull = false;
         if (leaf_beta(t, nl, S, Pn) <= ten_tau) {
             const int m = cnt[(int64_t)t.a * nl + t.c];
-            cull = pred[i] + 0.5f * log10f((float)m) < log10_budget;
+            cull = pred[i] + log10f((float)m) < log10_budget;
         }
         keep[i] = cull ? 0 : 1;
     }

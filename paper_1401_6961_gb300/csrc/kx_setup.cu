@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "kx_dw.cuh"
 #include "kx_internal.cuh"
 
 namespace kx {
@@ -1035,6 +1036,27 @@ __global__ void __launch_bounds__(256) k_dmma_probe(double* __restrict__ out, in
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Double-word FP32 multiply-add chains (kx_dw.cuh), eight independent
+// chains per thread; x <- x * a + b converges, so the values stay finite.
+// Counted as 2 FLOPs per double-word multiply-add (the FP64-equivalent
+// rate of the double-word kernels).
+__global__ void __launch_bounds__(256) k_dw_probe(float2* __restrict__ out, int iters, float ah, float al,
+                                                  float bh, float bl) {
+    const dw a(ah, al), b(bh, bl);
+    dw x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = dw((float)(threadIdx.x + k) * 1e-3f, 0.f);
+#pragma unroll 2
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = dw_fma(x[k], a, b);
+    }
+    dw s = x[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) s = dw_add(s, x[k]);
+    out[blockIdx.x * blockDim.x + threadIdx.x] = make_float2(s.hi, s.lo);
+}
+
 int peak_probe(int device, int precision, double* gflops) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
@@ -1042,7 +1064,9 @@ int peak_probe(int device, int precision, double* gflops) {
         return KX_ECUDA;
     }
     const int blocks = prop.multiProcessorCount * 8, threads = 256;
-    const int iters = precision == KX_FP64 ? 1 << 12 : (precision == KX_PROBE_FP64_MMA ? 1 << 10 : 1 << 17);
+    const int iters = precision == KX_FP64 ? 1 << 12
+                      : precision == KX_PROBE_FP64_MMA ? 1 << 10
+                      : precision == KX_PROBE_DW ? 1 << 14 : 1 << 17;
     void* out = nullptr;
     if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1058,6 +1082,8 @@ int peak_probe(int device, int precision, double* gflops) {
             k_fma_probe<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-6);
         else if (precision == KX_PROBE_FP64_MMA)
             k_dmma_probe<<<blocks, threads>>>((double*)out, iters, 1e-3, 1e-3);
+        else if (precision == KX_PROBE_DW)
+            k_dw_probe<<<blocks, threads>>>((float2*)out, iters, 0.9999f, 1e-11f, 1e-4f, 3e-12f);
         else
             k_fma_probe<float><<<blocks, threads>>>((float*)out, iters, 0.9999f, 1e-4f);
         cudaEventRecord(e1);

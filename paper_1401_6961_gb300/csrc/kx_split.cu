@@ -7,11 +7,12 @@
 // S_cd its Eq. 8 bound and eps32 = 2^-24.  The constants are per
 // angular-momentum class, measured on GB300 by evaluating single shell
 // quartets (single-shell leaves, pairwise distinct K blocks) in FP32 and in
-// FP64 and taking max|dK_block| / (eps32 beta) over about 2,000 quartets per
-// class of a water cluster in the medium basis, their bounds spread over
-// ten decades (paper_1401_6961_gb300/calibrate.py repeats the measurement).
-// c_max is 1.5 times the largest ratio seen; c_rms the root-mean-square
-// ratio.
+// FP64 and taking max|dK_block| / (eps32 beta) over 2,000-2,500 quartets
+// per class of (H2O)16 in the medium basis, their bounds spread over ten
+// decades (`python -m paper_1401_6961_gb300.calibrate` repeats the
+// measurement and prints these tables).  c_max is 1.5 times the largest
+// ratio seen (1.2 to 6.2 by class); c_rms the root-mean-square ratio (0.16
+// to 0.76).
 //
 // For a candidate split s, the FP32 quartets of a K shell block (a,c) are
 // its quartets with beta <= s, so its error is bounded by
@@ -37,26 +38,26 @@ namespace {
 
 // per class ((la*3 + lb)*3 + lc)*3 + ld
 const float CMAX[NCLASS] = {
-    6.45f, 5.33f, 7.25f, 7.11f, 3.66f, 7.71f, 6.65f, 4.36f, 4.44f,
-    5.33f, 4.73f, 2.9f, 3.55f, 4.11f, 3.85f, 6.6f, 3.18f, 2.73f,
-    5.15f, 4.24f, 2.1f, 4.04f, 2.68f, 2.05f, 9.37f, 3.36f, 2.54f,
-    8.33f, 5.58f, 4.32f, 5.0f, 5.37f, 4.05f, 8.55f, 5.61f, 4.16f,
-    5.43f, 2.73f, 2.21f, 3.81f, 3.78f, 2.49f, 4.26f, 3.29f, 2.36f,
-    4.01f, 2.23f, 2.25f, 3.79f, 2.99f, 2.09f, 5.5f, 2.43f, 3.58f,
-    8.06f, 5.49f, 5.71f, 6.27f, 9.37f, 5.27f, 6.62f, 7.35f, 5.04f,
-    4.15f, 4.75f, 2.89f, 4.44f, 4.04f, 3.08f, 6.14f, 2.75f, 1.82f,
-    4.24f, 2.52f, 1.88f, 4.19f, 2.97f, 2.15f, 5.3f, 2.41f, 3.06f,
+    6.4f, 5.28f, 7.2f, 7.06f, 3.61f, 7.66f, 6.6f, 4.31f, 4.39f,
+    5.28f, 4.68f, 2.85f, 3.5f, 4.06f, 3.8f, 6.55f, 3.13f, 2.68f,
+    5.1f, 4.19f, 2.05f, 3.99f, 2.63f, 2.0f, 9.32f, 3.31f, 2.49f,
+    8.28f, 5.53f, 4.27f, 4.95f, 5.32f, 4.0f, 8.5f, 5.56f, 4.11f,
+    5.38f, 2.68f, 2.16f, 3.76f, 3.73f, 2.44f, 4.21f, 3.24f, 2.31f,
+    3.96f, 2.18f, 2.2f, 3.74f, 2.94f, 2.04f, 5.45f, 2.38f, 3.53f,
+    8.01f, 5.44f, 5.66f, 6.22f, 9.32f, 5.22f, 6.57f, 7.3f, 4.99f,
+    4.1f, 4.7f, 2.84f, 4.39f, 3.99f, 3.03f, 6.09f, 2.7f, 1.77f,
+    4.19f, 2.47f, 1.83f, 4.14f, 2.92f, 2.1f, 5.25f, 2.36f, 3.01f,
 };
 const float CRMS[NCLASS] = {
-    1.03f, 0.705f, 0.702f, 1.14f, 0.605f, 0.582f, 1.19f, 0.71f, 0.727f,
-    0.727f, 0.428f, 0.376f, 0.626f, 0.383f, 0.299f, 0.737f, 0.391f, 0.358f,
-    0.596f, 0.36f, 0.297f, 0.513f, 0.328f, 0.249f, 0.651f, 0.346f, 0.325f,
-    1.03f, 0.619f, 0.639f, 0.866f, 0.611f, 0.533f, 1.11f, 0.654f, 0.567f,
-    0.634f, 0.358f, 0.336f, 0.614f, 0.36f, 0.315f, 0.657f, 0.39f, 0.352f,
-    0.64f, 0.307f, 0.282f, 0.461f, 0.301f, 0.241f, 0.583f, 0.303f, 0.267f,
-    1.16f, 0.755f, 0.677f, 0.944f, 0.646f, 0.529f, 1.14f, 0.662f, 0.625f,
-    0.701f, 0.474f, 0.351f, 0.688f, 0.383f, 0.308f, 0.727f, 0.409f, 0.347f,
-    0.538f, 0.326f, 0.316f, 0.636f, 0.319f, 0.261f, 0.622f, 0.312f, 0.313f,
+    0.654f, 0.399f, 0.395f, 0.681f, 0.402f, 0.372f, 0.762f, 0.434f, 0.441f,
+    0.416f, 0.247f, 0.218f, 0.357f, 0.246f, 0.195f, 0.451f, 0.257f, 0.227f,
+    0.358f, 0.221f, 0.175f, 0.32f, 0.209f, 0.158f, 0.397f, 0.216f, 0.192f,
+    0.642f, 0.37f, 0.338f, 0.561f, 0.389f, 0.32f, 0.683f, 0.396f, 0.359f,
+    0.414f, 0.232f, 0.211f, 0.384f, 0.239f, 0.2f, 0.424f, 0.248f, 0.241f,
+    0.358f, 0.186f, 0.163f, 0.288f, 0.201f, 0.157f, 0.368f, 0.199f, 0.183f,
+    0.732f, 0.439f, 0.404f, 0.639f, 0.447f, 0.336f, 0.763f, 0.441f, 0.41f,
+    0.428f, 0.271f, 0.219f, 0.411f, 0.248f, 0.2f, 0.459f, 0.26f, 0.22f,
+    0.366f, 0.21f, 0.189f, 0.379f, 0.224f, 0.178f, 0.406f, 0.221f, 0.207f,
 };
 
 constexpr double EPS32 = 5.9604644775390625e-08;   // 2^-24

@@ -198,10 +198,9 @@ def learned_exchange(ex, P, model: Model, tau: float, budget: Optional[float] = 
 
     A leaf quartet of bound <= 10 tau is dropped when its predicted
     contribution, raised by the model's calibrated margin (else by
-    ``margin`` residual standard deviations) and multiplied by the square
-    root of the number of such quartets in its K block, is below ``budget``
-    (default tau / 10): the predicted root-sum-square of what any K block
-    loses stays below the budget."""
+    ``margin`` residual standard deviations) and multiplied by the number of
+    such quartets in its K block, is below ``budget`` (default tau / 10):
+    the predicted sum of what any K block loses stays below the budget."""
     torch = _torch()
     ctx = ex.ctx
     o = B.kx_default_opts(tau=tau, **opts)
@@ -211,7 +210,7 @@ def learned_exchange(ex, P, model: Model, tau: float, budget: Optional[float] = 
         B.kx_leaf_features(ctx, feat.data_ptr(), n)
     pred = predict(model.params, feat[:n], ex.device) if n else feat[:0, 0]
     lb = math.log10(0.1 * tau if budget is None else budget)
-    # the margin shifts every prediction up: pred + margin + log10(m)/2 < log10(budget)
+    # the margin shifts every prediction up: pred + margin + log10(m) < log10(budget)
     shift = model.margin if model.margin is not None else margin * model.residual_std
     kept = B.kx_cull_kept(ctx, pred.data_ptr(), tau, lb - shift) if n else 0
     if K is None:

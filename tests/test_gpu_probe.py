@@ -26,11 +26,15 @@ def test_probes_report_positive_rates(kx):
     f64 = kx.kx_peak_probe(0, kx.KX_FP64)
     f32 = kx.kx_peak_probe(0, kx.KX_MIXED)
     mma = kx.kx_peak_probe(0, kx.KX_PROBE_FP64_MMA)
-    print(f"FP64 FMA {f64:.0f} GFLOP/s, FP32 FMA {f32:.0f} GFLOP/s, FP64 DMMA {mma:.0f} GFLOP/s")
-    assert f64 > 0 and f32 > 0 and mma > 0
+    dw = kx.kx_peak_probe(0, kx.KX_PROBE_DW)
+    print(f"FP64 FMA {f64:.0f} GFLOP/s, FP32 FMA {f32:.0f} GFLOP/s, FP64 DMMA {mma:.0f} GFLOP/s, "
+          f"double-word FMA {dw:.0f} GFLOP/s")
+    assert f64 > 0 and f32 > 0 and mma > 0 and dw > 0
     assert f32 > 10 * f64
+    # a double-word FMA is about 15 FP32 instructions: well above the FP64 pipe on GB300
+    assert f64 < dw < f32
 
 
 def test_probe_rejects_unknown_kind(kx):
     with pytest.raises(kx.KxError):
-        kx.kx_peak_probe(0, 3)
+        kx.kx_peak_probe(0, 4)

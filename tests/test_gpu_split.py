@@ -53,7 +53,8 @@ def test_estimate_holds_for_the_chosen_split(kx, name, tau, leaf):
     Kb = ex(Pd, tau=tau, symmetric=1, precision=kx.KX_MIXED, split_budget=budget).clone()
     assert ex.stats.split_used == sp.split_used
     assert ex.stats.fp32_err_estimate == sp.fp32_err_estimate
-    assert (Kb - Km).abs().max().item() <= 1e-12
+    # (the planning pass changes the leaf chunking, and so the FP32 warp sums)
+    assert (Kb - Km).abs().max().item() <= 2 * sp.fp32_err_estimate
     if name == "water4":
         Kr, *_ = oracle.exchange_screened(sys_, P, tau, leaf_max=leaf)
         assert np.abs(Km.cpu().numpy() - Kr).max() <= 1e-8
