@@ -787,11 +787,12 @@ def run_ours(args):
 
 SWEEP_N = (64, 128, 256, 512)
 SWEEP_TAU = (1e-10, 1e-8, 1e-6)
-SWEEP_BUILD_S = 25.0      # time a build only when the count predicts at most this many seconds
-SWEEP_MAX_SHELL_Q = 2e12  # counts (traversal + count pass of the screen) stay within about 30 s
+SWEEP_BUILD_S = 200.0     # time a mixed build only when the count predicts at most this many seconds
+SWEEP_FP64_S = 60.0       # and the FP64 build of the same point at most this many
+SWEEP_MAX_SHELL_Q = 4e12  # counts (traversal + count pass of the screen) stay within about a minute
 SWEEP_MAX_LEAF_Q = 1.5e10  # and the frontier before the last level within a few tens of GB
 SWEEP_GROWTH = 2.5        # predicted survivors grow as n_fn^2.5 (measured: 1.7-2.6)
-RATE_MIXED, RATE_FP64 = 6e9, 1e9   # shell quartets/s of the (H2O)64 builds, for that prediction
+RATE_MIXED, RATE_FP64 = 8e9, 1e9   # shell quartets/s of the (H2O)64 builds, for that prediction
 
 
 def _event_ms(stream, fn):
@@ -850,7 +851,7 @@ def run_sweep(args):
             del P
             K = torch.empty_like(Pd)
             for tau in taus:
-                mixed = dict(tau=tau, precision=kx.KX_MIXED, split_threshold=SPLIT)
+                mixed = dict(tau=tau, precision=PRECISION[args.precision](kx), split_threshold=SPLIT)
                 ms_c, full = _event_ms(stream, lambda: ex.count(Pd, symmetric=0, **mixed))
                 last[(basis, tau)] = (sys_.n_fn, full.n_shell_quartets, full.n_leaf_quartets)
                 half = ex.count(Pd, symmetric=1, **mixed)
@@ -865,7 +866,7 @@ def run_sweep(args):
                     ms, _ = _event_ms(stream, lambda: ex(Pd, out=K, symmetric=1, **mixed))
                     row["mixed_ms"] = ms
                     row["mixed_quartets_per_s"] = q / (ms * 1e-3)
-                    if q / RATE_FP64 <= SWEEP_BUILD_S:
+                    if q / RATE_FP64 <= SWEEP_FP64_S:
                         Km = K.clone()
                         ms64, _ = _event_ms(stream, lambda: ex(Pd, out=K, symmetric=1, tau=tau,
                                                                precision=kx.KX_FP64))
@@ -893,7 +894,8 @@ def run_sweep(args):
                          "exponent_n_lg_n": float(np.polyfit(x, np.log([p[0] * math.log2(p[0]) for p in pts]),
                                                              1)[0])})
     print(json.dumps({"study": "sweep", "workload": "(H2O)_n at 1 g/cm^3, n = " + ",".join(map(str, ns)),
-                      "split_threshold": SPLIT, "leaf_max": args.leaf_max, "points": rows, "fits": fits}),
+                      "precision": args.precision, "split_threshold": SPLIT, "leaf_max": args.leaf_max,
+                      "points": rows, "fits": fits}),
           flush=True)
 
 
@@ -967,6 +969,49 @@ def run_learned(args):
                       "evaluation": evals}), flush=True)
 
 
+def run_symmetry(args):
+    """The symmetry cases of Eqs. 9-10 among the kept leaf quartets of
+    (H2O)_n builds (medium basis, tau = 1e-10, every K block): the shares of
+    full 4-fold blocks, blocks with coinciding index blocks and sparse
+    blocks, the kept quartets per canonical integral block, the share of
+    the ERI FLOPs that does not involve P, and the bound that gives on what
+    the further index swaps could save over the K-transpose half."""
+    import numpy as np
+    import torch
+
+    import paper_1401_6961_gb300 as kx
+    import workloads as wl
+    from paper_1401_6961_gb300 import symmetry
+
+    torch.cuda.set_device(0)
+    kx.load()
+    rows = []
+    for nw in [int(x) for x in args.sym_n.split(",")]:
+        sys_ = wl.water_sweep(nw, "medium") if nw != 64 else wl.water64(2)
+        P = wl.density(sys_, 5000 + nw) if nw != 64 else wl.workload("water64")[1]
+        ex = kx.Exchange(sys_, device=0, leaf_max=args.leaf_max)
+        Pd = torch.from_numpy(P).cuda()
+        ex(Pd, tau=TAU, symmetric=0, keep_worklist=1)
+        work = ex.worklist()
+        occ = symmetry.occurrence_counts(work)
+        # ERI FLOPs of the symmetric build by class, and their integral part
+        ex(Pd, tau=TAU, symmetric=1, profile=1)
+        prof = ex.profile()
+        n_cls = prof["n"][:81] + prof["n"][81:162] + prof["n"][162:]
+        f_int = symmetry.integral_share(n_cls)
+        tasks_sym = int((work[:, 0] <= work[:, 2]).sum())
+        reuse = occ["blocks"] / tasks_sym
+        row = {"n_water": nw, "n_fn": sys_.n_fn, "leaf_max": args.leaf_max, "tau": TAU, **occ,
+               "share_full": occ["full"] / occ["blocks"], "share_coincident": occ["coincident"] / occ["blocks"],
+               "share_sparse": occ["sparse"] / occ["blocks"], "tasks_symmetric": tasks_sym,
+               "canonical_blocks_per_symmetric_task": reuse, "eri_integral_flop_share": f_int,
+               "bound_eri_flops_saved": f_int * (1.0 - reuse)}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        ex.close()
+    print(json.dumps({"study": "symmetry", "points": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -991,7 +1036,8 @@ def main():
                     help="build every K block instead of the A <= C half and its mirror")
     ap.add_argument("--leaf-max", type=int, default=BENCH_LEAF,
                     help="bisection leaf size in functions (Eq. 1); the paper's CPU code used 10")
-    ap.add_argument("--study", choices=["sweep", "learned"], default=None,
+    ap.add_argument("--sym-n", default="16,32,64", help="water cluster sizes of the symmetry study")
+    ap.add_argument("--study", choices=["sweep", "learned", "symmetry"], default=None,
                     help="instead of the benchmark line: the (H2O)_n scaling sweep, or the learned-culling "
                          "evaluation (one JSON line each, per-point lines on stderr)")
     ap.add_argument("--sweep-n", default=",".join(map(str, SWEEP_N)))
@@ -1001,6 +1047,8 @@ def main():
     args = ap.parse_args()
     if args.study == "sweep":
         run_sweep(args)
+    elif args.study == "symmetry":
+        run_symmetry(args)
     elif args.study == "learned":
         run_learned(args)
     elif args.impl == "reference":

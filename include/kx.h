@@ -186,7 +186,7 @@ int kx_count(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, kx_stats
  * variant of the build's count pass sums, for a sample of K shell blocks
  * (every diagonal block, every pair of tree neighbours, 4 n_shell seeded
  * random blocks), the FP32 quartets' c_max beta and (c_rms beta)^2 in bins
- * of log2 beta.  The split is the largest tau * 2^k whose estimate
+ * of log2 beta.  The split is the largest tau * 2^(k/4) whose estimate
  * 5 eps32 max_ac sqrt(sum (c_rms beta)^2) over those blocks is at most
  * `budget`: st->split_used, st->fp32_err_estimate (that estimate) and
  * st->fp32_err_bound (eps32 max_ac sum c_max beta, the bound under the

@@ -53,8 +53,9 @@ struct ExpandArgs {
     double* work;
     const float* sflops;
     // statistics pass (split planning): for every FP32 quartet of a sampled
-    // K shell block (blkslot[(a,c)] >= 0), in bin j = floor(log2 beta -
-    // lbin0) clamped to [0, nbin): acc[(slot * nbin + j) * 2] += cmax[cls]
+    // K shell block (blkslot[(a,c)] >= 0), in bin j = floor((log2 beta -
+    // lbin0) * PLAN_BINS_PER_OCTAVE) clamped to [0, nbin):
+    // acc[(slot * nbin + j) * 2] += cmax[cls]
     // beta and acc[... + 1] += (crms[cls] beta)^2
     const int32_t* blkslot;
     double* blkacc;
@@ -70,7 +71,7 @@ __device__ __forceinline__ void block_stats(const ExpandArgs& p, float x, int st
     const int slot = __ldg(p.blkslot + t0 + (int64_t)a * ns + c);
     if (slot < 0) return;
     const int cls = stream - NCLASS;
-    const int j = min(max((int)floorf(x - p.lbin0), 0), p.nbin - 1);
+    const int j = min(max((int)floorf((x - p.lbin0) * PLAN_BINS_PER_OCTAVE), 0), p.nbin - 1);
     const double beta = (double)exp2f(x);
     double* acc = p.blkacc + ((int64_t)slot * p.nbin + j) * 2;
     atomicAdd(acc, (double)__ldg(p.cmax + cls) * beta);

@@ -29,6 +29,8 @@ constexpr int NPREC = 3;
 constexpr int NSTREAM = NPREC * NCLASS;
 // double-word kernels exist for the classes with la+lb+lc+ld <= DW_LMAX
 constexpr int DW_LMAX = 5;
+// split planning: bins of log2 beta per octave (candidate splits tau 2^(k/4))
+constexpr int PLAN_BINS_PER_OCTAVE = 4;
 __host__ __device__ constexpr int class_l(int cls) { return cls / 27 + (cls / 9) % 3 + (cls / 3) % 3 + cls % 3; }
 constexpr int NPAIRCLASS = 9;       // (la,lb)
 constexpr int MAX_LEVELS = 32;

@@ -20,10 +20,10 @@
 // and of root-mean-square size
 //     E_ac(s) = eps32 sqrt(sum_{q in (a,c), beta_q <= s} (c_rms beta_q)^2).
 // A statistics variant of the shell screen's count pass accumulates both
-// sums in bins of log2 beta for a sample of K shell blocks: every diagonal
-// block (a,a), every block (a, a+1) of neighbours in tree order, and 4
-// n_shell seeded random blocks.  The plan takes the largest split
-// s = tau 2^k whose 5-sigma estimate 5 max_ac E_ac(s) over the sampled
+// sums in quarter-octave bins of log2 beta for a sample of K shell blocks:
+// every diagonal block (a,a), every block (a, a+1) of neighbours in tree
+// order, and 4 n_shell seeded random blocks.  The plan takes the largest
+// split s = tau 2^(k/4) whose 5-sigma estimate 5 max_ac E_ac(s) over the sampled
 // blocks fits the budget, and reports that estimate and max_ac B_ac(s).
 #include <algorithm>
 #include <cmath>
@@ -99,7 +99,7 @@ int split_plan(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double
     Lcg g{0x9e3779b97f4a7c15ull ^ (uint64_t)n};
     for (int k = 0; k < 4 * n; ++k) add((int)(g.next() % (uint32_t)n), (int)(g.next() % (uint32_t)n));
     const double t0 = std::max(o->tau, TAU_FLOOR);
-    const int nbin = std::max(1, (int)std::ceil(std::log2(SPLIT_MAX / t0)));
+    const int nbin = std::max(1, (int)std::ceil(std::log2(SPLIT_MAX / t0) * PLAN_BINS_PER_OCTAVE));
     const size_t nacc = blocks.size() * (size_t)nbin * 2;
     if (!c->d_cmax) {
         KX_CUDA(c, cudaMalloc(&c->d_cmax, sizeof(CMAX)));
@@ -142,8 +142,9 @@ int split_plan(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double
     cudaFree(d_slot);
     cudaFree(d_acc);
     if (r != KX_OK) return r;
-    // bin j holds beta in [t0 2^j, t0 2^(j+1)) (the bottom bin everything
-    // below); the FP32 quartets of split s_k = t0 2^k are bins j < k
+    // bin j holds beta in [t0 2^(j/4), t0 2^((j+1)/4)) (the bottom bin
+    // everything below); the FP32 quartets of split s_k = t0 2^(k/4) are
+    // bins j < k
     std::vector<double> s1(blocks.size(), 0.0), sq(blocks.size(), 0.0);
     double best = 0.0, best_est = 0.0, best_bnd = 0.0;
     for (int k = 1; k <= nbin; ++k) {
@@ -156,7 +157,7 @@ int split_plan(kx_ctx* c, const double* P, int64_t ldp, const kx_opts* o, double
         }
         const double est = SIGMAS * EPS32 * std::sqrt(m2), bnd = EPS32 * m1;
         if (est > budget) break;
-        best = t0 * std::ldexp(1.0, k);
+        best = t0 * std::exp2((double)k / PLAN_BINS_PER_OCTAVE);
         best_est = est;
         best_bnd = bnd;
     }

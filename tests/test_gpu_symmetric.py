@@ -111,22 +111,28 @@ BENCH_LEAF = 16   # bisection leaf size of the benchmark builds
 
 def test_water64_symmetric_mixed_rows(kx):
     """The benchmark system in the benchmark's launch configuration (leaf
-    size 16, tuned shapes, captured build replayed, split 5e-4, symmetric):
-    sampled K rows against the oracle at the same leaf size, and the leaf
-    worklist of those rows against the oracle's traversal."""
+    size 16, tuned shapes, captured build replayed, double words above the
+    split, the split planned from an 8e-9 FP32 budget, symmetric): 16
+    sampled K-row shells (4 d, 6 p, 6 s) against the oracle at the same leaf
+    size, and the leaf worklist of those rows against the oracle's
+    traversal."""
     import torch
     sys_, P = wl.workload("water64")
     ex = kx.Exchange(sys_, leaf_max=BENCH_LEAF)
     Pd = torch.from_numpy(P).cuda()
     Kd = torch.empty_like(Pd)
-    opts = dict(tau=1e-10, precision=kx.KX_MIXED, split_threshold=5e-4, symmetric=1)
+    sp = ex.split_plan(Pd, 8e-9, tau=1e-10, symmetric=1)
+    assert sp.split_used > 0
+    opts = dict(tau=1e-10, precision=kx.KX_MIXED_DW, split_threshold=sp.split_used, symmetric=1)
     ex.autotune(Pd, out=Kd, **opts)
     ex.plan(Pd, Kd, **opts)
     Kd.zero_()
     ex.replay()
     torch.cuda.synchronize()
     K = Kd.cpu().numpy()
-    rows = [int(x) for x in np.random.default_rng(65).choice(sys_.n_shell, size=3, replace=False)]
+    L = np.asarray(sys_.shell_l)
+    rng = np.random.default_rng(65)
+    rows = [int(x) for l, k in ((2, 4), (1, 6), (0, 6)) for x in rng.choice(np.nonzero(L == l)[0], k, replace=False)]
     Kref, wref, nq, tree, s2 = oracle.exchange_screened(sys_, P, 1e-10, leaf_max=BENCH_LEAF, rows=rows)
     off = sys_.shell_offset
     idx = np.concatenate([np.arange(off[r], off[r + 1]) for r in rows])
