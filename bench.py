@@ -744,6 +744,11 @@ def run_ours(args):
                       "profile": "CUDA events around every class launch"},
             "stages_ms_eager": {"norms": ste.ms_norms, "traverse": ste.ms_traverse, "expand": ste.ms_expand,
                                 "eri": ste.ms_eri},
+            "shell_screen": {"candidates": int(ste.n_candidates), "ms_eager": ste.ms_expand,
+                             "candidates_per_s": ste.n_candidates / max(ste.ms_expand * 1e-3, 1e-12),
+                             "kept": int(ste.n_shell_quartets),
+                             "unit": "shell quartets of the kept leaf quartets, each tested against Eq. 8 "
+                                     "(count and write passes)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": kernel_name(kx, ex.ctx, s_dom),
