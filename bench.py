@@ -323,13 +323,34 @@ def run_reference(args):
             f"stratified by angular momentum, {args.ref_rows} per step ({len(timed)} timed rows, "
             f"{sum(t for _, _, t in timed):.1f} s), extrapolated per angular momentum to the full build; host "
             f"{host_cpu()}")
+    single = single_thread_row(args.workload, min(timed, key=lambda x: x[2]), args.leaf_max)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(sys_, "fp64", args.workload, leaf_max=args.leaf_max),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+                             "single_thread": single},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def single_thread_row(workload: str, row, leaf_max: int, timeout_s: float = 240.0):
+    """The cheapest timed K-row shell again, in a process whose OpenMP runs
+    one thread: its time against the all-core time of the same row."""
+    r, l, t_all = row
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle, workloads as wl; oracle.build(); "
+            "s, P = wl.workload(%r); t0 = time.perf_counter(); "
+            "oracle.exchange_screened(s, P, %r, leaf_max=%d, rows=[%d]); print(time.perf_counter() - t0)"
+            % (ROOT, workload, TAU, leaf_max, r))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=timeout_s)
+        t1 = float(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return {"row_shell": r, "l": l, "unavailable": f"single-thread run failed or exceeded {timeout_s:.0f} s"}
+    return {"row_shell": r, "l": l, "seconds_1_thread": t1, "seconds_all_threads": t_all,
+            "parallel_speedup": t1 / t_all}
 
 
 def workload_config(sys_, precision, name, symmetric=True, leaf_max=10, split=SPLIT, parallelism="replicas"):
@@ -493,6 +514,49 @@ def run_batch(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def learned_leg(kx, ex, Pd, K64, stream, opts, leaf_max, ws):
+    """The learned-culling build of the benchmark system next to the plain
+    mixed build: training traces of medium-basis (H2O)4 and (H2O)8, margin
+    from a held-out (H2O)12 (99.9 % quantile of the residual), then one
+    warm-up and one timed culled build."""
+    import torch
+
+    import workloads as wl
+    from paper_1401_6961_gb300 import learned
+
+    tau = opts["tau"]
+    t0 = time.perf_counter()
+
+    def tr_of(n_w, seed, samples):
+        s = wl.water_cluster(n_w, seed, "medium")
+        e = kx.Exchange(s, device=ex.device, stream=stream, leaf_max=leaf_max)
+        t = learned.traces(e, torch.from_numpy(wl.density(s, 1000 + seed)).to(Pd.device), tau,
+                           max_samples=samples, seed=1)
+        e.close()
+        return t
+    tr = tr_of(4, 104, 20000) + tr_of(8, 108, 20000)
+    model = learned.train(tr, epochs=200, lr=3e-3, batch=4096)
+    model = learned.calibrate(model, tr_of(12, 112, 20000), q=0.999)
+    set_up_s = time.perf_counter() - t0
+    K = torch.empty_like(Pd)
+    learned.learned_exchange(ex, Pd, model, tau, K=K, **{k: v for k, v in opts.items() if k != "tau"})
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, info = learned.learned_exchange(ex, Pd, model, tau, K=K, **{k: v for k, v in opts.items() if k != "tau"})
+    e1.record(stream)
+    torch.cuda.synchronize(Pd.device)
+    ms = e0.elapsed_time(e1)
+    return {"value": ws * 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": 1,
+            "launch": "eager (traversal, features, BF16 inference, cull, ERI stage)",
+            "leaf_quartets": info["leaf_quartets"], "leaf_quartets_kept": info["leaf_quartets_kept"],
+            "leaf_quartets_cullable": info["cullable"], "shell_quartets": info["shell_quartets"],
+            "max_abs_dK_vs_fp64": float((K - K64).abs().max().item()),
+            "training": {"traces": int(len(tr.targets)), "loss_first": model.losses[0],
+                         "loss_last": model.losses[-1], "margin_decades": model.margin,
+                         "set_up_s": set_up_s}}
 
 
 def run_ours(args):
@@ -702,6 +766,17 @@ def run_ours(args):
                "launch": "captured graph, replayed",
                "max_abs_dK_vs_fp64": float((Kd - K64).abs().max().item()) if fp64 else None}
 
+    # mixed precision + learned culling (the target build of the learned
+    # direction): the network is trained and its margin calibrated on small
+    # clusters of the same basis at the same tau and leaf size (untimed),
+    # then the culled build -- traversal, features, BF16 inference, cull and
+    # the ERI stage -- runs eagerly
+    lrn = None
+    if args.learned and not sharded and args.fp64_steps > 0:
+        lrn = learned_leg(kx, ex, Pd, K64, stream, nomix, args.leaf_max, ws)
+        lrn["speedup_vs_fp64_plain"] = lrn["value"] / fp64["value"]
+        lrn["shell_quartets_plain_mixed"] = int(quartets)
+
     # end to end through the host-buffer entry point (pinned host P and K)
     e2e = None
     if args.e2e_steps > 0:
@@ -773,6 +848,7 @@ def run_ours(args):
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "max_abs_dK_vs_fp64": diff,
             "mixed_fp64_above_split": lit,
+            "mixed_learned": lrn,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -1035,6 +1111,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-rows", type=int, default=2, help="K-row shells per oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned-culling build of the benchmark system")
     ap.add_argument("--replicas", action="store_true",
                     help="under torchrun, every rank builds the whole K instead of its row-block shard")
     ap.add_argument("--no-symmetric", action="store_true",

@@ -190,6 +190,30 @@ def test_learned_culling_is_safe_on_water256(kx, trained):
     ex.close()
 
 
+def test_learned_culling_in_symmetric_mixed_builds(kx, trained):
+    """The learned build with the options of the benchmark's build
+    (symmetric traversal, mixed precision, double words above the split):
+    it traverses only K blocks with A <= C, mirrors the rest, and stays
+    within 1e-8 of the plain FP64 build of every K block."""
+    import torch
+    from paper_1401_6961_gb300 import learned
+    model, _ = trained
+    tau = 1e-8
+    sys_ = wl.water_cluster(16, 16, "small")
+    P = torch.from_numpy(wl.density(sys_, 1016)).cuda()
+    ex = kx.Exchange(sys_)
+    K64 = ex(P, tau=tau).clone()
+    full = ex.stats.n_leaf_quartets
+    K1, info = learned.learned_exchange(ex, P, model, tau, symmetric=1, precision=kx.KX_MIXED_DW,
+                                        split_threshold=5e-4)
+    err = float((K1 - K64).abs().max())
+    print(f"symmetric learned build: leaf quartets {info['leaf_quartets']} of {full}, kept "
+          f"{info['leaf_quartets_kept']}, max|dK| {err:.2e}")
+    assert info["leaf_quartets"] < 0.6 * full
+    assert err <= 1e-8
+    ex.close()
+
+
 def test_cull_never_drops_quartets_above_ten_tau(kx, trained):
     import torch
     model, _ = trained
