@@ -104,9 +104,12 @@ struct WarpTables {
     float pbd[STAGE * STAGE];    // log2 ||P_bd||, [ib][id]
     float mb[STAGE];             // max over a of log2 S_ab, per b
     float md[STAGE];             // max over c of log2 S_cd, per d
+    float ma[STAGE];             // max over b of log2 S_ab, per a
+    float mc[STAGE];             // max over d of log2 S_cd, per c
     uint8_t cab[STAGE * STAGE];  // pair class la*3+lb
     uint8_t ccd[STAGE * STAGE];
     uint8_t kl[STAGE * STAGE];   // (b,d) pairs that can pass for some (a,c): ib*16+id
+    uint8_t rl[STAGE * STAGE];   // rows (a,c) that can pass for some kept (b,d): ia*16+ic
 };
 
 // Decides one candidate and returns its stream (-1 = culled).  The pair
@@ -221,7 +224,8 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                 tb.pbd[ib * STAGE + id] = __ldg(p.plog + t0 + (int64_t)(b0 + ib) * ns + d0 + id);
             }
             __syncwarp();
-            // column maxima for the (b,d) pre-filter
+            // column maxima for the (b,d) pre-filter, row maxima for the
+            // (a,c) pre-filter
             if (lane < nb) {
                 float m = -INFINITY;
                 for (int ia = 0; ia < na; ++ia) m = fmaxf(m, tb.sab[ia * STAGE + lane]);
@@ -231,6 +235,16 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                 float m = -INFINITY;
                 for (int ic = 0; ic < nc; ++ic) m = fmaxf(m, tb.scd[ic * STAGE + lane]);
                 tb.md[lane] = m;
+            }
+            if (lane >= 16 && lane - 16 < na) {
+                float m = -INFINITY;
+                for (int ib = 0; ib < nb; ++ib) m = fmaxf(m, tb.sab[(lane - 16) * STAGE + ib]);
+                tb.ma[lane - 16] = m;
+            }
+            if (lane >= 16 && lane - 16 < nc) {
+                float m = -INFINITY;
+                for (int id = 0; id < nd; ++id) m = fmaxf(m, tb.scd[(lane - 16) * STAGE + id]);
+                tb.mc[lane - 16] = m;
             }
             __syncwarp();
             // (b,d) pairs that can pass for some (a,c), kept in (b,d) order:
@@ -253,10 +267,31 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
             }
             __syncwarp();
             if (nk == 0) continue;
-            // sweep (row, k), row = (a,c), k = (b,d) in the compacted list,
-            // k fastest: one flat index so every lane has work
-            const int rows = na * nc;
-            const int total2 = rows * nk;
+            // rows (a,c) that can pass for some kept (b,d), in (a,c) order:
+            // log2 bound max_b S_ab + max_kept ||P_bd|| + max_d S_cd, with the
+            // same margin; in a symmetric diagonal block only a <= c
+            float mp = -INFINITY;
+            for (int k = lane; k < nk; k += 32) mp = fmaxf(mp, tb.pbd[(tb.kl[k] >> 4) * STAGE + (tb.kl[k] & 15)]);
+            for (int d = 16; d > 0; d >>= 1) mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, d));
+            int nr = 0;
+            for (int r0 = 0; r0 < na * nc; r0 += 32) {
+                const int r = r0 + lane;
+                bool ok = false;
+                int ia = 0, ic = 0;
+                if (r < na * nc) {
+                    ia = fdiv(r, mc);
+                    ic = r - ia * nc;
+                    ok = !(diag && ia > ic) &&
+                         (!p.screen || tb.ma[ia] + mp + tb.mc[ic] >= p.ltau - 2.f * LOG_MARGIN);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) tb.rl[nr + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(ia * STAGE + ic);
+                nr += __popc(bal);
+            }
+            __syncwarp();
+            // sweep (row, k) over the two compacted lists, k fastest: one
+            // flat index so every lane has work
+            const int total2 = nr * nk;
             const Div dk(nk);
             for (int base = 0; base < total2; base += 32) {
                 const unsigned idx = base + lane;
@@ -265,18 +300,16 @@ k_expand(ExpandArgs p, int64_t* __restrict__ bin, Quartet* __restrict__ rec, uns
                 if (idx < (unsigned)total2) {
                     const unsigned row = fdiv(idx, dk);
                     const int k = idx - row * nk;
-                    const int ia = fdiv(row, mc);
-                    const int ic = row - ia * nc;
+                    const int ac = tb.rl[row];
+                    const int ia = ac >> 4, ic = ac & 15;
                     const int bd = tb.kl[k];
                     const int ib = bd >> 4, id = bd & 15;
                     const float sab = tb.sab[ia * STAGE + ib], scd = tb.scd[ic * STAGE + id];
                     const float x = sab + tb.pbd[ib * STAGE + id] + scd;
                     const int cls = tb.cab[ia * STAGE + ib] * 9 + tb.ccd[ic * STAGE + id];
-                    if (!(diag && ia > ic)) {
-                        stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns,
-                                               pab, pcd);
-                        if (STATS) block_stats(p, x, stream, t0, ns, a0 + ia, c0 + ic);
-                    }
+                    stream = decide<WRITE>(p, x, sab, scd, a0 + ia, b0 + ib, c0 + ic, d0 + id, cls, t0, ns, pab,
+                                           pcd);
+                    if (STATS) block_stats(p, x, stream, t0, ns, a0 + ia, c0 + ic);
                 }
                 emit<WRITE>(stream, pab, pcd, lane, scount, rec, end, err, p.sflops, wsum);
             }
