@@ -142,7 +142,9 @@ def test_random_shells_all_classes(kx, seed):
     K0 = oracle.exchange_direct(sys_, P)
     for leaf_max in (1, 6):
         K, ex = _gpu_k(kx, sys_, P, leaf_max=leaf_max, tau=0.0)
-        assert np.abs(K - K0).max() <= TOL64 * max(1.0, np.abs(K0).max())
+        err = np.abs(K - K0).max()
+        print(f"seed {seed} leaf {leaf_max}: max|dK| {err:.2e}, max|K| {np.abs(K0).max():.2f}")
+        assert err <= TOL64
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
@@ -198,7 +200,7 @@ def test_random_shells_fp64_shared_memory_variant(kx, seed, variant):
     with pytest.raises(kx.KxError):
         kx.kx_set_launch_shape(ex.ctx, 0, 128, 0, 1)      # (ss|ss) has one kernel
     K = ex(torch.from_numpy(P).cuda(), tau=0.0).cpu().numpy()
-    assert np.abs(K - K0).max() <= TOL64 * max(1.0, np.abs(K0).max())
+    assert np.abs(K - K0).max() <= TOL64
     ex.close()
 
 
