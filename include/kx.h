@@ -118,13 +118,15 @@ typedef struct {
     double ms_eri;               /* ERI evaluation + contraction */
     double ms_eri_kernel_max;    /* longest single ERI class launch */
     double ms_total;
-    double split_used;           /* KX_MIXED: the split threshold of the build */
-    double fp32_err_bound;       /* KX_MIXED: c_max eps32 * (largest sum over one K shell block
-                                    of the FP32 quartets' bounds beta), a bound on max|dK|
-                                    from FP32 rounding under the per-quartet error model */
-    double fp32_err_estimate;    /* KX_MIXED: c_rms eps32 * (largest root-sum-square over one
-                                    K shell block of the FP32 quartets' beta), the expected
-                                    size of that error for independent roundings */
+    double split_used;           /* KX_MIXED(_DW): the split threshold of the build (the
+                                    planner's choice when split_budget > 0) */
+    double fp32_err_bound;       /* split_budget > 0: eps32 * (largest sum over one sampled K shell
+                                    block of c_max[class] * beta of its FP32 quartets), a
+                                    bound on max|dK| from FP32 rounding under the
+                                    per-quartet error model */
+    double fp32_err_estimate;    /* split_budget > 0: 5 eps32 * sqrt(largest sum over one sampled K
+                                    shell block of (c_rms[class] * beta)^2), a 5-sigma
+                                    estimate of that error for independent roundings */
 } kx_stats;
 
 /* Fills the defaults: tau = 1e-10, split 1e-5, FP64, shell screen on,
