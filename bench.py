@@ -334,7 +334,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def single_thread_row(workload: str, row, leaf_max: int, timeout_s: float = 240.0):
+def single_thread_row(workload: str, row, leaf_max: int, timeout_s: float = 120.0):
     """The cheapest timed K-row shell again, in a process whose OpenMP runs
     one thread: its time against the all-core time of the same row."""
     r, l, t_all = row
