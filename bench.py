@@ -5,15 +5,20 @@ One step = one complete exchange build K = sum (mu lam|nu sig) P_{lam sig}
 (P norms and pyramid, pair tables, hextree traversal with the Eq. 8 metric
 query, shell screen, ERI evaluation and contraction) of the seeded
 (H2O)_64 cluster at 1 g/cm^3, medium basis (1984 functions, 1024 shells),
-tau = 1e-10, leaves of at most 16 functions, replayed from one captured CUDA graph (after an untimed
-autotuning build and the capture).  The headline is the mixed-precision
-build (FP32 ERIs for quartets with beta <= split, FP64 above), next to the
-plain FP64 build of the same system; both stay within max|dK| <= 1e-8 of
-the FP64 path.
+tau = 1e-10, leaves of at most 16 functions, replayed from one captured
+CUDA graph (after an untimed split plan, autotuning build and capture).
+The headline is the mixed-precision build: FP32 ERIs for the quartets with
+beta <= split, double-word FP32 above it (FP64 for the classes without a
+double-word kernel), the split chosen from an FP32 error budget.  Next to
+it the line carries the plain FP64 build of the same system, the literal
+split build (FP64 above the split) and the learned-culling build, each
+with its max|dK| against the FP64 build.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
-Under torchrun every rank builds its own K (replicas: the build of one
-system is not split across GPUs), and the value counts all ranks' builds.
+Under torchrun the ranks split one build by K row-block shards and sum K
+with one all-reduce per step; ``--replicas`` gives every rank a whole
+build instead.  ``--study`` runs the scaling sweep, the learned-culling
+evaluation or the symmetry-case count instead of the benchmark.
 """
 from __future__ import annotations
 
